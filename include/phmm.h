@@ -1,0 +1,176 @@
+/*
+ * phmm.h -- C ABI of the GB300 (sm_103a) batched Pair-HMM library (libphmm.so).
+ *
+ * The library scores read/haplotype pairs with the Pair-HMM forward algorithm of
+ * gpuPairHMM (Schmidt et al., arXiv 2411.11547), Sec. II-A:
+ *   Eq. 1  M(i,j) = lambda(i,j) (alpha_i M(i-1,j-1) + beta (I(i-1,j-1) + D(i-1,j-1)))
+ *   Eq. 2  I(i,j) = delta_i M(i-1,j) + eps I(i-1,j)
+ *   Eq. 3  D(i,j) = zeta_i M(i,j-1) + eps D(i,j-1)
+ *   init   M(i,0)=I(i,0)=D(i,0)=0, M(0,j)=I(0,j)=0, D(0,j)=1/n
+ *   Eq. 4  lambda(i,j) = 1-Q_i if r_i == h_j else Q_i/3
+ *   result L = sum_j M(m,j) + I(m,j), returned as log10 L,
+ * and gives the adjoint of log10 L with respect to the per-base Phred qualities and the
+ * gap-continuation penalty.  Transition probabilities come from Phred values (Sec. III-A
+ * names the inputs; the conversion is this library's reading):
+ *   Q_i = 10^(-bq_i/10), delta_i = 10^(-iq_i/10), zeta_i = 10^(-dq_i/10),
+ *   eps = 10^(-gcp/10), beta = 1 - eps, alpha_i = 1 - (delta_i + zeta_i)
+ *   (alpha_mode 1: alpha_i = 1 - 10^(-(iq_i+dq_i)/10)).
+ * 'N' on either side matches every base; bases are ASCII A C G T N, either case.
+ *
+ * Conventions shared by every call:
+ *   - Every data pointer in phmm_batch and every output pointer is DEVICE memory owned by
+ *     the caller.  The library never frees or retains caller memory beyond the plan.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.
+ *   - Return value: PHMM_OK (0) or a negative PHMM_E* code.  No exception crosses the ABI,
+ *     no kernel traps, and no call spins without a bound.
+ *   - Calls are thread-compatible: one plan must not be used from two host threads at once.
+ */
+#ifndef PHMM_H
+#define PHMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define PHMM_OK 0
+#define PHMM_EINVAL -1   /* bad argument: offsets, lengths, bases, quals, gcp, pair ids */
+#define PHMM_ETOOLONG -2 /* a read longer than PHMM_MAX_READ_LEN */
+#define PHMM_ENOMEM -3   /* workspace smaller than phmm_workspace_bytes() */
+#define PHMM_ECUDA -4    /* a CUDA runtime call failed; see phmm_last_cuda_error() */
+#define PHMM_ESTATE -5   /* call out of order (e.g. backward on a plan never run forward) */
+
+#define PHMM_MAX_READ_LEN 512 /* longest read (rows) one wavefront group holds */
+
+/* ---- per-pair flags written by phmm_forward ---------------------------------------- */
+#define PHMM_FLAG_FP32 1       /* result from the FP32 wavefront (|err| <= 1e-3 log10) */
+#define PHMM_FLAG_RESCUED64 2  /* FP32 result underflowed: recomputed in FP64          */
+#define PHMM_FLAG_EXTENDED 4   /* recomputed with per-lane power-of-two exponents       */
+#define PHMM_FLAG_INVALID 8    /* invalid pair (bad ids or data): output is NaN         */
+
+/* ---- quality dtypes ------------------------------------------------------------------ */
+#define PHMM_QUAL_U8 0  /* uint8 Phred values (forward only)                  */
+#define PHMM_QUAL_F32 1 /* float Phred values, continuous (differentiable)    */
+
+/*
+ * A batch of reads, haplotypes and the pairs to score (Sec. II-A: batches B_q = (R_q, H_q);
+ * Sec. III-A: reads carry per-base quality scores plus insertion and deletion gap
+ * qualities).  All arrays are device memory; the plan keeps the pointers (not copies), so
+ * the caller keeps them alive and unchanged while the plan is used.
+ */
+typedef struct phmm_batch {
+  int64_t n_reads;            /* R >= 1 */
+  int64_t n_haps;             /* H >= 1 */
+  int64_t n_pairs;            /* P >= 0 */
+  const uint8_t *read_bases;  /* [sum m] ASCII bases, reads concatenated */
+  const void *base_q;         /* [sum m] Phred base qualities, dtype qual_dtype */
+  const void *ins_q;          /* [sum m] Phred insertion gap-open qualities */
+  const void *del_q;          /* [sum m] Phred deletion gap-open qualities */
+  int32_t qual_dtype;         /* PHMM_QUAL_U8 or PHMM_QUAL_F32 */
+  int32_t alpha_mode;         /* 0: alpha = 1-(delta+zeta)  1: alpha = 1-10^(-(iq+dq)/10) */
+  const int64_t *read_off;    /* [R+1] read r = read_bases[read_off[r] .. read_off[r+1]) */
+  const uint8_t *hap_bases;   /* [sum n] ASCII bases, haplotypes concatenated */
+  const int64_t *hap_off;     /* [H+1] */
+  const int32_t *pair_read;   /* [P] read index of each pair */
+  const int32_t *pair_hap;    /* [P] haplotype index of each pair */
+  double gcp;                 /* Phred gap-continuation penalty, > 0 */
+} phmm_batch;
+
+/* First-line (bulk) arithmetic of the forward pass. */
+#define PHMM_FIRST_PLAIN32 0 /* FP32, initial constant 2^120 (rescue below 1e-28 scaled) */
+#define PHMM_FIRST_EXT32 1   /* FP32 with per-lane power-of-two exponents: never underflows */
+
+/*
+ * Launch options.  phmm_options_default() fills the recommended values; fields may then be
+ * changed.  A NULL options pointer means the defaults.
+ */
+typedef struct phmm_options {
+  int32_t first_line;  /* PHMM_FIRST_PLAIN32 or PHMM_FIRST_EXT32 */
+  int32_t rescue;      /* 1: FP64 rescue of pairs below the FP32 threshold; 0: none */
+  int32_t binning;     /* 1: length binning + packing; 0: one fixed (lanes, rows) group */
+  int32_t lanes;       /* fixed group when binning == 0: lanes per pair, 4/8/16/32 */
+  int32_t rows;        /* fixed group when binning == 0: rows per lane, 4/8/12/16/20 */
+  int32_t persistent;  /* 1: persistent work-queue kernels; 0: one warp group per item */
+  int32_t use_graph;   /* 1: replay the launch sequence from a captured CUDA graph */
+  int32_t warps_per_block; /* 0 = automatic */
+  int32_t bin_rows[PHMM_MAX_READ_LEN / 4 + 1]; /* optional tuned table (see phmm_tune) */
+  int32_t bin_table_valid; /* 1 if bin_rows holds a tuned table */
+} phmm_options;
+
+void phmm_options_default(phmm_options *opt);
+
+typedef struct phmm_plan phmm_plan;
+
+/*
+ * Validate a batch and build a plan.  Runs one validation kernel on `stream` and waits for
+ * it (the only host synchronisation of the library): read and haplotype offsets must be
+ * non-decreasing from 0, every read and haplotype non-empty, bases in {A,C,G,T,N} (either
+ * case), Phred values finite-or-+inf and >= 0 with delta+zeta <= 1 (alpha_mode 0), pair ids
+ * in range, gcp > 0.  Returns PHMM_EINVAL / PHMM_ETOOLONG on bad input (no plan is
+ * created), PHMM_OK otherwise with *plan set.  The plan keeps the batch pointers.
+ */
+int phmm_plan_create(const phmm_batch *batch, const phmm_options *opt, void *stream,
+                     phmm_plan **plan);
+
+/* Bytes of device workspace phmm_forward / phmm_backward need (256-byte aligned start). */
+size_t phmm_workspace_bytes(const phmm_plan *plan);
+
+/* Plan facts: total read bases, total haplotype bases, sum over pairs of m*n (Eq. 5). */
+int phmm_plan_info(const phmm_plan *plan, int64_t *sum_m, int64_t *sum_n, int64_t *cells);
+
+/*
+ * Forward pass: out_log10[p] = log10 P(read | haplotype) for every pair p (device double
+ * [P]) and out_flags[p] (device uint8 [P], PHMM_FLAG_*).  Asynchronous on `stream`; no host
+ * synchronisation.  ws: device workspace of at least phmm_workspace_bytes(plan) bytes,
+ * 256-byte aligned, used as scratch (contents need not be preserved between calls except
+ * that phmm_backward reads what the latest phmm_forward on the same ws left there).
+ * Returns PHMM_ENOMEM if ws_bytes is too small, PHMM_EINVAL for NULL/misaligned pointers.
+ */
+int phmm_forward(phmm_plan *plan, void *ws, size_t ws_bytes, double *out_log10,
+                 uint8_t *out_flags, void *stream);
+
+/*
+ * Adjoint: given dL[p] = d(loss)/d(log10 L_p) (device double [P]), writes
+ *   d_base_q, d_ins_q, d_del_q : device float [sum m], d(loss)/d(Phred) summed over the
+ *                                pairs that share each read (overwritten, FP64-accumulated);
+ *   d_gcp                      : device double [1], d(loss)/d(gcp) summed over all pairs.
+ * Invalid pairs contribute nothing.  Requires a preceding phmm_forward with the same plan and
+ * ws (PHMM_ESTATE otherwise).  Asynchronous on `stream`.
+ */
+int phmm_backward(phmm_plan *plan, void *ws, size_t ws_bytes, const double *dL,
+                  float *d_base_q, float *d_ins_q, float *d_del_q, double *d_gcp,
+                  void *stream);
+
+void phmm_plan_destroy(phmm_plan *plan);
+
+const char *phmm_status_str(int status);
+
+/* The cudaError_t of the most recent PHMM_ECUDA return on this host thread. */
+int phmm_last_cuda_error(void);
+
+/*
+ * Kernel-time instrumentation: number of kernel launches the latest phmm_forward /
+ * phmm_backward on this plan issued (graph nodes count as launches), and the elapsed time of
+ * the FP32 wavefront kernels and of the FP64 rescue kernels of the latest forward, from CUDA
+ * events recorded on the launching stream.  Only a forward run without a CUDA graph
+ * (use_graph = 0) records those events; otherwise, or before the work has finished, both
+ * times are -1.  For throughput reporting only.
+ */
+int phmm_plan_launch_count(const phmm_plan *plan, int which /* 0 fwd, 1 bwd */);
+int phmm_plan_wavefront_ms(phmm_plan *plan, float *ms_fp32, float *ms_rescue);
+
+/*
+ * Arithmetic-pipe probe (roofline denominators): lane multiply-adds per second sustained
+ * by one kernel on the current device.  kind 0 = FP32 FFMA, 1 = packed fma.rn.f32x2
+ * (counted as two lane operations), 2 = FP64 DFMA.  Allocates and frees a small buffer.
+ */
+int phmm_probe_pipe(int kind, int iters, double *lane_ops_per_s, double *ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PHMM_H */

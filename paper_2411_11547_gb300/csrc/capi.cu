@@ -1,0 +1,576 @@
+// C ABI of libphmm: plans, workspace layout, the forward launch sequence and CUDA graphs.
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+#include "fwd_inst.cuh"
+#include "phmm_internal.cuh"
+
+namespace phmm {
+
+int launch_validate(const phmm_batch &b, int64_t sum_m, int64_t sum_n, unsigned *err,
+                    unsigned long long *cells, cudaStream_t s);
+int launch_prep(const phmm_batch &b, int64_t sum_m, float beta32, RowParams *rp,
+                uint8_t *rcode, uint8_t *hcode, cudaStream_t s, int *launches);
+int launch_binning(const phmm_batch &b, const CfgTable &tab, int32_t *key, int32_t *counts,
+                   int32_t *offsets, int32_t *cursor, int32_t *grp_begin, int32_t *grp_count,
+                   int32_t *order, cudaStream_t s, int *launches);
+int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, float *diq,
+                     float *ddq, double *dgcp, cudaStream_t s, int *launches);
+size_t bwd_workspace_bytes(const phmm_plan *pl);
+int bwd_default_cfg(int m);
+
+static thread_local int g_last_cuda = 0;
+
+static int cuda_fail(cudaError_t e) {
+  g_last_cuda = (int)e;
+  return PHMM_ECUDA;
+}
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+static size_t table_warp_bytes(int K, int elem) {
+  const int vw = 16 / elem, units = K * elem / 16;
+  const int LS = (units % 2 == 1) ? K : K + vw;
+  return (size_t)kCodes * 32 * LS * elem;
+}
+
+static FwdKernel get32(int cfg, bool ext) {
+  const int L = cfg_lanes(cfg), K = cfg_rows(cfg);
+  if (L <= 8) return ext ? fwd32_ext_lo(L, K) : fwd32_plain_lo(L, K);
+  return ext ? fwd32_ext_hi(L, K) : fwd32_plain_hi(L, K);
+}
+
+size_t fwd32_smem(int cfg, int block) { return (block / 32) * table_warp_bytes(cfg_rows(cfg), 4); }
+size_t fwd64_smem(int cfg64, int block) {
+  return (block / 32) * table_warp_bytes(rows64(cfg64), 8);
+}
+
+static std::once_flag g_attr_once;
+static void set_attrs() {
+  for (int cfg = 0; cfg < kNumCfg32; ++cfg)
+    for (int e = 0; e < 2; ++e) {
+      FwdKernel k = get32(cfg, e);
+      if (k) cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  227 * 1024);
+    }
+  for (int c = 0; c < kNumCfg64; ++c)
+    for (int e = 0; e < 2; ++e) {
+      FwdKernel k = fwd64_table(rows64(c), e);
+      if (k) cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  227 * 1024);
+    }
+}
+
+int fwd32_blocks_per_sm(int cfg, bool ext, int block) {
+  std::call_once(g_attr_once, set_attrs);
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, get32(cfg, ext), block,
+                                                fwd32_smem(cfg, block));
+  return nb;
+}
+int fwd64_blocks_per_sm(int cfg64, bool ext, int block) {
+  std::call_once(g_attr_once, set_attrs);
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd64_table(rows64(cfg64), ext), block,
+                                                fwd64_smem(cfg64, block));
+  return nb;
+}
+
+int launch_fwd32(int cfg, bool ext, int grid, int block, cudaStream_t s, const FwdArgs &a) {
+  std::call_once(g_attr_once, set_attrs);
+  FwdKernel k = get32(cfg, ext);
+  if (!k) return (int)cudaErrorInvalidValue;
+  k<<<grid, block, fwd32_smem(cfg, block), s>>>(a);
+  return (int)cudaGetLastError();
+}
+int launch_fwd64(int cfg64, bool ext, int grid, int block, cudaStream_t s, const FwdArgs &a) {
+  std::call_once(g_attr_once, set_attrs);
+  FwdKernel k = fwd64_table(rows64(cfg64), ext);
+  if (!k) return (int)cudaErrorInvalidValue;
+  k<<<grid, block, fwd64_smem(cfg64, block), s>>>(a);
+  return (int)cudaGetLastError();
+}
+
+// Default read-length -> group table: the smallest lanes x rows group holding m, preferring
+// few lanes (short wavefront ramp) and many rows per lane (per-step overhead amortised).
+static int default_cfg_of_m(int m) {
+  struct G { int cap, L, K; };
+  static const G order[] = {{16, 4, 4},   {32, 4, 8},   {48, 4, 12},  {64, 4, 16},
+                            {80, 4, 20},  {96, 8, 12},  {128, 8, 16}, {160, 8, 20},
+                            {192, 16, 12}, {256, 16, 16}, {320, 16, 20}, {384, 32, 12},
+                            {512, 32, 16}};
+  for (const G &g : order)
+    if (m <= g.cap) {
+      int li = g.L == 4 ? 0 : g.L == 8 ? 1 : g.L == 16 ? 2 : 3;
+      int ki = g.K / 4 - 1;
+      return li * 5 + ki;
+    }
+  return kNumCfg32 - 1;
+}
+
+}  // namespace phmm
+
+using namespace phmm;
+
+struct WsLayout {
+  size_t rp, rcode, hcode, key, order, zero, zero_bytes, counts, ctr32, ctr64, ctrx, rcnt, xcnt,
+      offsets, cursor, grp_begin, grp_count, rlist, xlist, bwd, total;
+};
+
+struct phmm_plan {
+  phmm_batch b;
+  phmm_options o;
+  int64_t sum_m = 0, sum_n = 0, cells = 0, pair_rows = 0, n_max = 0;
+  int max_m = 0;
+  int cfg_of_m[PHMM_MAX_READ_LEN + 1];
+  int bwd_cfg_of_m[PHMM_MAX_READ_LEN + 1];
+  std::vector<int> used_cfgs, bwd_used;
+  WsLayout L;
+  int sms = 0;
+  float eps32 = 0, beta32 = 0;
+  double eps64 = 0, beta64 = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  void *g_ws = nullptr, *g_out = nullptr, *g_flags = nullptr;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  bool fwd_done = false;
+  bool timed = false;  // the latest forward recorded the timing events
+  int launches_fwd = 0, launches_bwd = 0;
+  void *bwd_state = nullptr;  // owned by the backward translation unit
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static void make_layout(phmm_plan *pl) {
+  WsLayout &L = pl->L;
+  const int64_t P = std::max<int64_t>(pl->b.n_pairs, 1);
+  const size_t nkeys = (size_t)kNumCfg32 * kNBuckets;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  L.rp = take(sizeof(RowParams) * std::max<int64_t>(pl->sum_m, 1));
+  L.rcode = take(std::max<int64_t>(pl->sum_m, 1));
+  L.hcode = take((size_t)hap_start(pl->sum_n, pl->b.n_haps) + 64);
+  L.key = take(4 * P);
+  L.order = take(4 * P);
+  // region zeroed at the start of every forward
+  L.zero = o;
+  L.counts = o;
+  o += 4 * nkeys;
+  L.ctr32 = o;
+  o += 4 * kNumCfg32;
+  L.ctr64 = o;
+  o += 4 * kNumCfg64;
+  L.ctrx = o;
+  o += 4 * kNumCfg64;
+  L.rcnt = o;
+  o += 4 * kNumCfg64;
+  L.xcnt = o;
+  o += 4 * kNumCfg64;
+  o = align256(o);
+  L.zero_bytes = o - L.zero;
+  L.offsets = take(4 * nkeys);
+  L.cursor = take(4 * nkeys);
+  L.grp_begin = take(4 * kNumCfg32);
+  L.grp_count = take(4 * kNumCfg32);
+  L.rlist = take((size_t)4 * P * kNumCfg64);
+  L.xlist = take((size_t)4 * P * kNumCfg64);
+  L.bwd = o;
+  L.total = o;
+}
+
+extern "C" {
+
+void phmm_options_default(phmm_options *opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->first_line = PHMM_FIRST_EXT32;
+  opt->rescue = 1;
+  opt->binning = 1;
+  opt->lanes = 8;
+  opt->rows = 16;
+  opt->persistent = 1;
+  opt->use_graph = 1;
+  opt->warps_per_block = 4;
+  opt->bin_table_valid = 0;
+}
+
+const char *phmm_status_str(int s) {
+  switch (s) {
+    case PHMM_OK: return "ok";
+    case PHMM_EINVAL: return "invalid argument";
+    case PHMM_ETOOLONG: return "read longer than PHMM_MAX_READ_LEN";
+    case PHMM_ENOMEM: return "workspace too small";
+    case PHMM_ECUDA: return "CUDA error";
+    case PHMM_ESTATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+int phmm_last_cuda_error(void) { return g_last_cuda; }
+
+static bool valid_group(int L, int K) {
+  return (L == 4 || L == 8 || L == 16 || L == 32) && K >= 4 && K <= 20 && K % 4 == 0;
+}
+
+int phmm_plan_create(const phmm_batch *batch, const phmm_options *opt, void *stream,
+                     phmm_plan **out) {
+  if (!batch || !out) return PHMM_EINVAL;
+  *out = nullptr;
+  const phmm_batch &b = *batch;
+  phmm_options o;
+  if (opt)
+    o = *opt;
+  else
+    phmm_options_default(&o);
+  if (b.n_reads < 1 || b.n_haps < 1 || b.n_pairs < 0) return PHMM_EINVAL;
+  if (b.n_reads > INT32_MAX || b.n_haps > INT32_MAX || b.n_pairs > INT32_MAX) return PHMM_EINVAL;
+  if (!b.read_bases || !b.base_q || !b.ins_q || !b.del_q || !b.read_off || !b.hap_bases ||
+      !b.hap_off)
+    return PHMM_EINVAL;
+  if (b.n_pairs > 0 && (!b.pair_read || !b.pair_hap)) return PHMM_EINVAL;
+  if (b.qual_dtype != PHMM_QUAL_U8 && b.qual_dtype != PHMM_QUAL_F32) return PHMM_EINVAL;
+  if (b.alpha_mode != 0 && b.alpha_mode != 1) return PHMM_EINVAL;
+  if (!(b.gcp > 0.0) || !std::isfinite(b.gcp)) return PHMM_EINVAL;
+  if (o.first_line != PHMM_FIRST_PLAIN32 && o.first_line != PHMM_FIRST_EXT32) return PHMM_EINVAL;
+  if (!o.binning && !valid_group(o.lanes, o.rows)) return PHMM_EINVAL;
+  (void)cudaGetLastError();  // drop a stale error left by an unrelated call
+  if (o.warps_per_block <= 0) o.warps_per_block = 4;
+  if (o.warps_per_block > 8) return PHMM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+
+  // offsets to the host: monotone from 0, non-empty sequences, read length bound
+  std::vector<int64_t> ro(b.n_reads + 1), ho(b.n_haps + 1);
+  CK(cudaMemcpyAsync(ro.data(), b.read_off, 8 * ro.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(ho.data(), b.hap_off, 8 * ho.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (ro[0] != 0 || ho[0] != 0) return PHMM_EINVAL;
+  int max_m = 0;
+  for (int64_t r = 0; r < b.n_reads; ++r) {
+    const int64_t m = ro[r + 1] - ro[r];
+    if (m <= 0) return PHMM_EINVAL;
+    if (m > PHMM_MAX_READ_LEN) return PHMM_ETOOLONG;
+    max_m = std::max<int>(max_m, (int)m);
+  }
+  for (int64_t h = 0; h < b.n_haps; ++h)
+    if (ho[h + 1] - ho[h] <= 0 || ho[h + 1] - ho[h] > INT32_MAX / 2) return PHMM_EINVAL;
+  const int64_t sum_m = ro[b.n_reads], sum_n = ho[b.n_haps];
+
+  // device checks: bases, Phred values, pair ids; and the cell count of Eq. 5
+  void *dbuf = nullptr;
+  CK(cudaMalloc(&dbuf, 64));
+  CK(cudaMemsetAsync(dbuf, 0, 64, s));
+  unsigned *err = (unsigned *)dbuf;
+  unsigned long long *cells = (unsigned long long *)((char *)dbuf + 8);
+  int rc = launch_validate(b, sum_m, sum_n, err, cells, s);
+  unsigned long long hbuf[3] = {0, 0, 0};
+  cudaError_t e2 = rc ? (cudaError_t)rc : cudaMemcpyAsync(hbuf, dbuf, 24, cudaMemcpyDeviceToHost, s);
+  if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(s);
+  cudaFree(dbuf);
+  if (e2 != cudaSuccess) return cuda_fail(e2);
+  if ((unsigned)hbuf[0] != 0) return PHMM_EINVAL;
+
+  phmm_plan *pl = new (std::nothrow) phmm_plan();
+  if (!pl) return PHMM_ENOMEM;
+  pl->b = b;
+  pl->o = o;
+  pl->sum_m = sum_m;
+  pl->sum_n = sum_n;
+  pl->cells = (int64_t)hbuf[1];
+  pl->pair_rows = (int64_t)hbuf[2];
+  pl->max_m = max_m;
+  for (int64_t h = 0; h < b.n_haps; ++h) pl->n_max = std::max<int64_t>(pl->n_max, ho[h + 1] - ho[h]);
+  pl->eps64 = std::pow(10.0, -b.gcp / 10.0);
+  pl->beta64 = 1.0 - pl->eps64;
+  pl->eps32 = (float)pl->eps64;
+  pl->beta32 = (float)pl->beta64;
+  for (int m = 0; m <= PHMM_MAX_READ_LEN; ++m) {
+    int c = default_cfg_of_m(std::max(m, 1));
+    if (o.bin_table_valid) {
+      const int e = o.bin_rows[(std::max(m, 1) + 3) / 4];
+      if (e >= 0 && e < kNumCfg32 && cfg_lanes(e) * cfg_rows(e) >= m) c = e;
+    }
+    pl->cfg_of_m[m] = c;
+  }
+  if (o.binning) {
+    std::vector<char> used(kNumCfg32, 0);
+    for (int64_t r = 0; r < b.n_reads; ++r) used[pl->cfg_of_m[ro[r + 1] - ro[r]]] = 1;
+    for (int c = 0; c < kNumCfg32; ++c)
+      if (used[c]) pl->used_cfgs.push_back(c);
+  }
+  {
+    for (int m = 0; m <= PHMM_MAX_READ_LEN; ++m) pl->bwd_cfg_of_m[m] = bwd_default_cfg(std::max(m, 1));
+    std::vector<char> used(kNumCfg32, 0);
+    for (int64_t r = 0; r < b.n_reads; ++r) used[pl->bwd_cfg_of_m[ro[r + 1] - ro[r]]] = 1;
+    for (int c = 0; c < kNumCfg32; ++c)
+      if (used[c]) pl->bwd_used.push_back(c);
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&pl->sms, cudaDevAttrMultiProcessorCount, dev);
+  make_layout(pl);
+  pl->L.total = pl->L.bwd + bwd_workspace_bytes(pl);
+  cudaError_t ce = cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking);
+  for (int i = 0; i < 3 && ce == cudaSuccess; ++i) ce = cudaEventCreate(&pl->ev[i]);
+  if (ce != cudaSuccess) {
+    phmm_plan_destroy(pl);
+    return cuda_fail(ce);
+  }
+  *out = pl;
+  return PHMM_OK;
+}
+
+size_t phmm_workspace_bytes(const phmm_plan *pl) { return pl ? pl->L.total : 0; }
+
+int phmm_plan_info(const phmm_plan *pl, int64_t *sum_m, int64_t *sum_n, int64_t *cells) {
+  if (!pl) return PHMM_EINVAL;
+  if (sum_m) *sum_m = pl->sum_m;
+  if (sum_n) *sum_n = pl->sum_n;
+  if (cells) *cells = pl->cells;
+  return PHMM_OK;
+}
+
+void phmm_plan_destroy(phmm_plan *pl) {
+  if (!pl) return;
+  if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
+  for (auto &e : pl->ev)
+    if (e) cudaEventDestroy(e);
+  if (pl->cap) cudaStreamDestroy(pl->cap);
+  delete pl;
+}
+
+}  // extern "C"
+
+// The whole forward pass as a stream-ordered launch sequence (capturable).
+// `timed`: record the plan's events around the FP32 and rescue kernels (not under capture).
+static int enqueue_forward(phmm_plan *pl, char *ws, double *out, uint8_t *flags,
+                           cudaStream_t s, bool timed) {
+  const WsLayout &L = pl->L;
+  const phmm_batch &b = pl->b;
+  const phmm_options &o = pl->o;
+  int launches = 0;
+  CK(cudaMemsetAsync(ws + L.zero, 0, L.zero_bytes, s));
+  RowParams *rp = (RowParams *)(ws + L.rp);
+  uint8_t *rcode = (uint8_t *)(ws + L.rcode), *hcode = (uint8_t *)(ws + L.hcode);
+  int rc = launch_prep(b, pl->sum_m, pl->beta32, rp, rcode, hcode, s, &launches);
+  if (rc) return cuda_fail((cudaError_t)rc);
+  int32_t *order = (int32_t *)(ws + L.order);
+  int32_t *grp_begin = (int32_t *)(ws + L.grp_begin), *grp_count = (int32_t *)(ws + L.grp_count);
+  if (o.binning && b.n_pairs > 0) {
+    CfgTable tab;
+    for (int m = 0; m <= PHMM_MAX_READ_LEN; ++m) tab.cfg[m] = (int8_t)pl->cfg_of_m[m];
+    rc = launch_binning(b, tab, (int32_t *)(ws + L.key),
+                        (int32_t *)(ws + L.counts), (int32_t *)(ws + L.offsets),
+                        (int32_t *)(ws + L.cursor), grp_begin, grp_count, order, s, &launches);
+    if (rc) return cuda_fail((cudaError_t)rc);
+  }
+
+  FwdArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.pair_read = b.pair_read;
+  a.pair_hap = b.pair_hap;
+  a.read_off = b.read_off;
+  a.hap_off = b.hap_off;
+  a.rp = rp;
+  a.rcode = rcode;
+  a.hcode = hcode;
+  a.bq = b.base_q;
+  a.iq = b.ins_q;
+  a.dq = b.del_q;
+  a.qual_f32 = b.qual_dtype == PHMM_QUAL_F32;
+  a.alpha_mode = b.alpha_mode;
+  a.n_reads = b.n_reads;
+  a.n_haps = b.n_haps;
+  a.out = out;
+  a.flags = flags;
+  a.eps32 = pl->eps32;
+  a.beta32 = pl->beta32;
+  a.eps64 = pl->eps64;
+  a.beta64 = pl->beta64;
+  a.rescue = o.rescue;
+  int32_t *rcnt = (int32_t *)(ws + L.rcnt), *xcnt = (int32_t *)(ws + L.xcnt);
+  for (int k = 0; k < kNumCfg64; ++k) {
+    a.rescue_list[k] = (int32_t *)(ws + L.rlist) + (size_t)k * std::max<int64_t>(b.n_pairs, 1);
+  }
+  a.rescue_count = rcnt;
+  const bool ext = o.first_line == PHMM_FIRST_EXT32;
+  a.mode = ext ? 1 : 0;
+  const int block = 32 * o.warps_per_block;
+
+  if (timed) CK(cudaEventRecord(pl->ev[0], s));
+  if (b.n_pairs > 0) {
+    if (o.binning) {
+      for (int cfg : pl->used_cfgs) {
+        FwdArgs c = a;
+        c.list = order;
+        c.offset_dev = grp_begin + cfg;
+        c.count_dev = grp_count + cfg;
+        c.counter = (int32_t *)(ws + L.ctr32) + cfg;
+        c.persistent = 1;
+        const int grid = pl->sms * std::max(1, fwd32_blocks_per_sm(cfg, ext, block));
+        rc = launch_fwd32(cfg, ext, grid, block, s, c);
+        if (rc) return cuda_fail((cudaError_t)rc);
+        ++launches;
+      }
+    } else {
+      const int li = o.lanes == 4 ? 0 : o.lanes == 8 ? 1 : o.lanes == 16 ? 2 : 3;
+      const int cfg = li * 5 + (o.rows / 4 - 1);
+      FwdArgs c = a;
+      c.count = b.n_pairs;
+      const int G = 32 / o.lanes;
+      const int64_t items = (b.n_pairs + G - 1) / G;
+      int grid;
+      if (o.persistent) {
+        c.persistent = 1;
+        c.counter = (int32_t *)(ws + L.ctr32) + cfg;
+        grid = pl->sms * std::max(1, fwd32_blocks_per_sm(cfg, ext, block));
+      } else {
+        grid = (int)((items + o.warps_per_block - 1) / o.warps_per_block);
+      }
+      rc = launch_fwd32(cfg, ext, grid, block, s, c);
+      if (rc) return cuda_fail((cudaError_t)rc);
+      ++launches;
+    }
+  }
+  if (timed) CK(cudaEventRecord(pl->ev[1], s));
+  if (o.rescue && b.n_pairs > 0) {
+    // FP64 with K0 = 2^1020; failures go on to the per-lane-exponent FP64 kernel.
+    for (int tier = 0; tier < 2; ++tier) {
+      for (int k = 0; k < kNumCfg64; ++k) {
+        FwdArgs c = a;
+        c.mode = tier == 0 ? 2 : 3;
+        c.list = (tier == 0 ? (int32_t *)(ws + L.rlist) : (int32_t *)(ws + L.xlist)) +
+                 (size_t)k * std::max<int64_t>(b.n_pairs, 1);
+        c.count_dev = (tier == 0 ? rcnt : xcnt) + k;
+        c.counter = (int32_t *)(ws + (tier == 0 ? L.ctr64 : L.ctrx)) + k;
+        c.persistent = 1;
+        c.rescue = tier == 0 ? 1 : 0;
+        for (int q = 0; q < kNumCfg64; ++q)
+          c.rescue_list[q] = (int32_t *)(ws + L.xlist) + (size_t)q * std::max<int64_t>(b.n_pairs, 1);
+        c.rescue_count = xcnt;
+        const int grid = pl->sms * std::max(1, fwd64_blocks_per_sm(k, tier == 1, block));
+        rc = launch_fwd64(k, tier == 1, grid, block, s, c);
+        if (rc) return cuda_fail((cudaError_t)rc);
+        ++launches;
+      }
+    }
+  }
+  if (timed) CK(cudaEventRecord(pl->ev[2], s));
+  pl->launches_fwd = launches;
+  return PHMM_OK;
+}
+
+extern "C" {
+
+int phmm_forward(phmm_plan *pl, void *ws, size_t ws_bytes, double *out, uint8_t *flags,
+                 void *stream) {
+  if (!pl || !ws || (pl->b.n_pairs > 0 && (!out || !flags))) return PHMM_EINVAL;
+  if (((uintptr_t)ws & 255) != 0) return PHMM_EINVAL;
+  if (ws_bytes < pl->L.total) return PHMM_ENOMEM;
+  cudaStream_t s = (cudaStream_t)stream;
+  (void)cudaGetLastError();  // drop a stale error left by an unrelated call
+  pl->timed = false;
+  int rc;
+  if (pl->o.use_graph) {
+    if (!pl->gexec || pl->g_ws != ws || pl->g_out != out || pl->g_flags != flags) {
+      if (pl->gexec) {
+        cudaGraphExecDestroy(pl->gexec);
+        pl->gexec = nullptr;
+      }
+      CK(cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal));
+      rc = enqueue_forward(pl, (char *)ws, out, flags, pl->cap, false);
+      cudaGraph_t g = nullptr;
+      cudaError_t ce = cudaStreamEndCapture(pl->cap, &g);
+      if (rc != PHMM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      if (ce != cudaSuccess) return cuda_fail(ce);
+      ce = cudaGraphInstantiate(&pl->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (ce != cudaSuccess) return cuda_fail(ce);
+      pl->g_ws = ws;
+      pl->g_out = out;
+      pl->g_flags = flags;
+    }
+    CK(cudaGraphLaunch(pl->gexec, s));
+    rc = PHMM_OK;
+  } else {
+    rc = enqueue_forward(pl, (char *)ws, out, flags, s, true);
+    pl->timed = rc == PHMM_OK;
+  }
+  if (rc == PHMM_OK) pl->fwd_done = true;
+  return rc;
+}
+
+int phmm_backward(phmm_plan *pl, void *ws, size_t ws_bytes, const double *dL, float *dbq,
+                  float *diq, float *ddq, double *dgcp, void *stream) {
+  if (!pl || !ws || !dgcp) return PHMM_EINVAL;
+  if (pl->sum_m > 0 && (!dbq || !diq || !ddq)) return PHMM_EINVAL;
+  if (pl->b.n_pairs > 0 && !dL) return PHMM_EINVAL;
+  if (((uintptr_t)ws & 255) != 0) return PHMM_EINVAL;
+  if (ws_bytes < pl->L.total) return PHMM_ENOMEM;
+  if (!pl->fwd_done) return PHMM_ESTATE;
+  (void)cudaGetLastError();
+  int launches = 0;
+  int rc = bwd_enqueue_impl(pl, (char *)ws, dL, dbq, diq, ddq, dgcp, (cudaStream_t)stream,
+                            &launches);
+  pl->launches_bwd = launches;
+  if (rc) return cuda_fail((cudaError_t)rc);
+  return PHMM_OK;
+}
+
+int phmm_plan_launch_count(const phmm_plan *pl, int which) {
+  if (!pl) return -1;
+  return which == 0 ? pl->launches_fwd : pl->launches_bwd;
+}
+
+int phmm_plan_wavefront_ms(phmm_plan *pl, float *ms_fp32, float *ms_rescue) {
+  if (!pl) return PHMM_EINVAL;
+  float a = -1.f, r = -1.f;
+  if (pl->timed && cudaEventQuery(pl->ev[2]) == cudaSuccess) {
+    if (cudaEventElapsedTime(&a, pl->ev[0], pl->ev[1]) != cudaSuccess) a = -1.f;
+    if (cudaEventElapsedTime(&r, pl->ev[1], pl->ev[2]) != cudaSuccess) r = -1.f;
+  }
+  if (ms_fp32) *ms_fp32 = a;
+  if (ms_rescue) *ms_rescue = r;
+  return PHMM_OK;
+}
+
+}  // extern "C"
+
+// Accessors used by the backward translation unit.
+namespace phmm {
+const phmm_batch &plan_batch(const phmm_plan *pl) { return pl->b; }
+const phmm_options &plan_options(const phmm_plan *pl) { return pl->o; }
+size_t plan_bwd_offset(const phmm_plan *pl) { return pl->L.bwd; }
+int64_t plan_sum_m(const phmm_plan *pl) { return pl->sum_m; }
+int plan_sms(const phmm_plan *pl) { return pl->sms; }
+void **plan_bwd_state(phmm_plan *pl) { return &pl->bwd_state; }
+size_t plan_layout_rp(const phmm_plan *pl) { return pl->L.rp; }
+size_t plan_layout_rcode(const phmm_plan *pl) { return pl->L.rcode; }
+size_t plan_layout_hcode(const phmm_plan *pl) { return pl->L.hcode; }
+double plan_eps64(const phmm_plan *pl) { return pl->eps64; }
+int64_t plan_n_max(const phmm_plan *pl) { return pl->n_max; }
+int64_t plan_pair_rows(const phmm_plan *pl) { return pl->pair_rows; }
+const int *plan_bwd_cfg_of_m(const phmm_plan *pl) { return pl->bwd_cfg_of_m; }
+const std::vector<int> &plan_bwd_used(const phmm_plan *pl) { return pl->bwd_used; }
+// 0 counts, 1 key, 2 offsets, 3 cursor, 4 grp_begin, 5 grp_count, 6 order, 7 ctr32
+size_t plan_layout_bin(const phmm_plan *pl, int which) {
+  const WsLayout &L = pl->L;
+  const size_t v[8] = {L.counts, L.key, L.offsets, L.cursor, L.grp_begin, L.grp_count, L.order,
+                       L.ctr32};
+  return v[which];
+}
+}  // namespace phmm

@@ -1,0 +1,435 @@
+// The Pair-HMM forward wavefront (Sec. III-B, redesigned for sm_103a).
+//
+// One pair is scored by a group of L lanes of a warp (G = 32/L pairs per warp).  Lane t
+// owns K consecutive rows (read positions) of the DP matrices and keeps M, I, D of its rows
+// in registers (Sec. III-B: full in-register recurrences).  At step s it computes column
+// j = s - t of its rows; the values of the row just above its strip, at columns j and
+// j-1, come from lane t-1 through __shfl_up_sync (Sec. III-B, Fig. 2), together with the
+// haplotype code of the column.  Lane 0 reads 16 haplotype codes per 128-bit load.
+//
+// Emission (Eq. 4) is staged in shared memory as E[c][row] = beta * lambda for the six codes
+// (A C G T N and "no column"), so one 128-bit load returns four rows' emissions for the
+// column's code (Sec. III-B: the |Sigma| x m emission table).  With beta folded into E and
+// alpha' = alpha/beta, Eq. 1 becomes M = E[h_j][i] * (alpha'_i M(i-1,j-1) + I(i-1,j-1) +
+// D(i-1,j-1)): 3 FP32 pipe operations, plus 2 for Eq. 2 and 2 for Eq. 3, 7 per cell.
+//
+// Reads shorter than L*K are padded at the TOP: pad rows carry the row-0 boundary down
+// unchanged (their I passes through with coefficient 1, their emissions are 0), so the last
+// row of the last lane is always row m and the result is the running sum of its M + I
+// (Sec. II-A result line).  The first real row takes I(0,j) = 0 through a zero I
+// coefficient, and M(1,j) = lambda * beta * D(0,j-1) through the boundary value
+// I + D = K0/n of the row above, which is the initialisation D(0,j) = 1/n times K0.
+//
+// Precision tiers (the FP64 rescue and per-lane exponents are not in the paper):
+//   plain: one initial constant K0 (2^120 in FP32, 2^1020 in FP64), exact by linearity;
+//   ext:   every 16 steps each lane renormalises its state by a power of two and tracks the
+//          exponent; incoming boundary values are converted by 2^(E_up - E_own).  Exact up
+//          to rounding because the recurrences are linear; never underflows.
+#pragma once
+#include <cmath>
+#include "phmm_internal.cuh"
+
+namespace phmm {
+
+template <typename T>
+struct Num;
+
+template <>
+struct Num<float> {
+  static constexpr float K0 = kK32;
+  static constexpr int kMinExp = -126, kMaxExp = 127;
+  __device__ __forceinline__ static int ilog2(float x) {
+    return ((__float_as_int(x) >> 23) & 0xff) - 127;
+  }
+  __device__ __forceinline__ static float exp2i(int d) {
+    if (d < kMinExp) return 0.f;
+    if (d > kMaxExp) d = kMaxExp;
+    return __int_as_float((d + 127) << 23);
+  }
+};
+
+template <>
+struct Num<double> {
+  static constexpr double K0 = kK64;
+  static constexpr int kMinExp = -1022, kMaxExp = 1023;
+  __device__ __forceinline__ static int ilog2(double x) {
+    return (int)((__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
+  }
+  __device__ __forceinline__ static double exp2i(int d) {
+    if (d < kMinExp) return 0.0;
+    if (d > kMaxExp) d = kMaxExp;
+    return __longlong_as_double((long long)(d + 1023) << 52);
+  }
+};
+
+// Start of haplotype h inside the code buffer: 16-byte aligned, with room for the NULLC
+// padding up to the next 16-byte boundary (closed form, so no scan is needed).
+__host__ __device__ __forceinline__ int64_t hap_start(int64_t hap_off_h, int64_t h) {
+  return (hap_off_h + 32 * h + 15) & ~(int64_t)15;
+}
+
+// Shared-memory row stride (elements) of one lane's emission rows: a lane's 16-byte chunks
+// must fall in distinct bank groups for 8 consecutive lanes, so the stride in 16-byte units
+// is odd.
+template <typename T, int K>
+struct TableGeom {
+  static constexpr int VW = 16 / sizeof(T);                 // elements per 128-bit load
+  static constexpr int units = K * (int)sizeof(T) / 16;
+  static constexpr int LS = (units % 2 == 1) ? K : K + VW;  // lane stride
+  static constexpr int CS = 32 * LS;                        // code-plane stride
+  static constexpr size_t warp_bytes = (size_t)kCodes * CS * sizeof(T);
+};
+
+template <typename T, int K>
+__device__ __forceinline__ void store_vec(T *dst, const T *v);
+template <>
+__device__ __forceinline__ void store_vec<float, 4>(float *dst, const float *v) {
+  *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void store_vec<double, 2>(double *dst, const double *v) {
+  *reinterpret_cast<double2 *>(dst) = make_double2(v[0], v[1]);
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void load_rows(const T *src, T (&e)[K]) {
+  constexpr int VW = 16 / sizeof(T);
+#pragma unroll
+  for (int r = 0; r < K; r += VW) {
+    if constexpr (sizeof(T) == 4) {
+      float4 v = *reinterpret_cast<const float4 *>(src + r);
+      e[r] = v.x;
+      e[r + 1] = v.y;
+      e[r + 2] = v.z;
+      e[r + 3] = v.w;
+    } else {
+      double2 v = *reinterpret_cast<const double2 *>(src + r);
+      e[r] = v.x;
+      e[r + 1] = v.y;
+    }
+  }
+}
+
+__device__ __forceinline__ double qual_at(const void *q, int f32, int64_t g) {
+  return f32 ? (double)reinterpret_cast<const float *>(q)[g]
+             : (double)reinterpret_cast<const uint8_t *>(q)[g];
+}
+
+// Row parameters of read position g: alpha' = alpha/beta, delta, zeta, Q.
+template <typename T>
+__device__ __forceinline__ void row_params(const FwdArgs &a, int64_t g, T &ap, T &dl, T &zt,
+                                           T &Q) {
+  if constexpr (sizeof(T) == 4) {
+    RowParams v = a.rp[g];
+    ap = v.x;
+    dl = v.y;
+    zt = v.z;
+    Q = v.w;
+  } else {
+    const double bq = qual_at(a.bq, a.qual_f32, g), iq = qual_at(a.iq, a.qual_f32, g),
+                 dq = qual_at(a.dq, a.qual_f32, g);
+    Q = exp10(-bq / 10.0);
+    dl = exp10(-iq / 10.0);
+    zt = exp10(-dq / 10.0);
+    const double al = a.alpha_mode ? 1.0 - exp10(-(iq + dq) / 10.0) : 1.0 - (dl + zt);
+    ap = al / a.beta64;
+  }
+}
+
+// Register state of one lane of the wavefront.
+template <typename T, int K>
+struct WfState {
+  T M[K], I[K], D[K];  // the lane's rows at its current column
+  T Md, Sd;            // row above the strip at the previous column: M and I + D
+  T acc;               // running sum of M + I of the lane's last row
+  T f;                 // 2^(E_up - E_own) (and the row bias) for values from the lane above
+  int E;               // per-lane exponent (per-lane-exponent tier)
+  int c;               // haplotype code of the lane's current column
+};
+
+// One wavefront step: lane t advances its K rows by one column (Eq. 1-3).
+// `in3` receives the boundary values (M, I, D of the row above at this column, in the
+// lane's own scale) for callers that record the step (the adjoint's recompute).
+template <typename T, int L, int K, bool EXT>
+__device__ __forceinline__ void wf_step(WfState<T, K> &st, int cu, int t, T bnd, T eps,
+                                        const T *tbl, const T (&ap)[K], const T (&dl)[K],
+                                        const T (&zt)[K], const T (&ei)[K], T (&in3)[3]) {
+  constexpr unsigned FULL = 0xffffffffu;
+  constexpr int CS = TableGeom<T, K>::CS;
+  const int cin = __shfl_up_sync(FULL, st.c, 1, L);
+  st.c = (t == 0) ? cu : cin;
+  T inM = __shfl_up_sync(FULL, st.M[K - 1], 1, L);
+  T inI = __shfl_up_sync(FULL, st.I[K - 1], 1, L);
+  T inD = __shfl_up_sync(FULL, st.D[K - 1], 1, L);
+  if (t == 0) {  // row 0 (or the last pad row): M = 0, I + D = K0 * D(0, j) carried in I
+    inM = 0;
+    inI = bnd;
+    inD = 0;
+  }
+  if constexpr (EXT) {
+    inM *= st.f;
+    inI *= st.f;
+    inD *= st.f;
+  }
+  in3[0] = inM;
+  in3[1] = inI;
+  in3[2] = inD;
+  T e[K];
+  load_rows<T, K>(tbl + st.c * CS, e);
+#pragma unroll
+  for (int r = K - 1; r >= 0; --r) {
+    const T md = r ? st.M[r - 1] : st.Md;
+    const T sd = r ? st.I[r - 1] + st.D[r - 1] : st.Sd;
+    st.D[r] = zt[r] * st.M[r] + eps * st.D[r];  // Eq. 3 (same row, previous column)
+    st.M[r] = e[r] * (ap[r] * md + sd);         // Eq. 1 (previous row, previous column)
+  }
+  st.I[0] = dl[0] * inM + ei[0] * inI;  // Eq. 2 (previous row, same column)
+#pragma unroll
+  for (int r = 1; r < K; ++r) st.I[r] = dl[r] * st.M[r - 1] + ei[r] * st.I[r - 1];
+  st.Md = inM;
+  st.Sd = inI + inD;
+  st.acc += st.M[K - 1] + st.I[K - 1];
+}
+
+// Per-lane renormalisation by a power of two (exact).  A lane that holds only zeros (the
+// wavefront has not reached it) takes the exponent that makes the next values from the lane
+// above arrive near 1.
+template <typename T, int L, int K, int kBias>
+__device__ __forceinline__ void wf_rescale(WfState<T, K> &st, int t) {
+  constexpr unsigned FULL = 0xffffffffu;
+  T mx = st.Md > st.Sd ? st.Md : st.Sd;
+#pragma unroll
+  for (int r = 0; r < K; ++r) mx = fmax(mx, fmax(st.M[r], fmax(st.I[r], st.D[r])));
+  if (t == L - 1) mx = fmax(mx, st.acc);
+  const bool zero = !(mx > (T)0);
+  if (!zero) {
+    const int En = st.E + Num<T>::ilog2(mx);
+    const T sc = Num<T>::exp2i(st.E - En);
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+      st.M[r] *= sc;
+      st.I[r] *= sc;
+      st.D[r] *= sc;
+    }
+    st.Md *= sc;
+    st.Sd *= sc;
+    st.acc *= sc;
+    st.E = En;
+  }
+  const T xb = fmax(st.M[K - 1], fmax(st.I[K - 1], st.D[K - 1]));
+  const int Eup = __shfl_up_sync(FULL, st.E, 1, L);
+  const T xbu = __shfl_up_sync(FULL, xb, 1, L);
+  if (zero && t > 0)
+    st.E = Eup - kBias * (K - 1) + (xbu > (T)0 ? Num<T>::ilog2(xbu) : 0);
+  st.f = Num<T>::exp2i(t == 0 ? -st.E : Eup - st.E - kBias * (K - 1));
+}
+
+template <typename T, int L, int K, bool EXT>
+__global__ void __launch_bounds__(128) wf_forward(const FwdArgs a) {
+  using G_ = TableGeom<T, K>;
+  constexpr int G = 32 / L;
+  constexpr int VW = G_::VW, LS = G_::LS, CS = G_::CS;
+  constexpr unsigned FULL = 0xffffffffu;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t = lane % L, sub = lane / L;
+  T *tbl = reinterpret_cast<T *>(smem_raw) + (size_t)warp * kCodes * CS + lane * LS;
+  const T eps = sizeof(T) == 4 ? (T)a.eps32 : (T)a.eps64;
+  const T beta = sizeof(T) == 4 ? (T)a.beta32 : (T)a.beta64;
+
+  const int64_t count = a.count_dev ? (int64_t)*a.count_dev : a.count;
+  const int64_t base = a.offset_dev ? (int64_t)*a.offset_dev : a.list_offset;
+  const int64_t nitems = (count + G - 1) / G;
+  const int wpb = blockDim.x >> 5;
+  int64_t item = (int64_t)blockIdx.x * wpb + warp;
+  bool first = true;
+
+  for (;;) {
+    if (a.persistent) {
+      int it = 0;
+      if (lane == 0) it = atomicAdd(a.counter, 1);
+      item = __shfl_sync(FULL, it, 0);
+    } else if (!first) {
+      break;
+    }
+    first = false;
+    if (item >= nitems) break;
+
+    // ---- this lane's pair --------------------------------------------------------------
+    const int64_t idx = item * G + sub;
+    const bool valid = idx < count;
+    int32_t p = -1;
+    bool bad = false;
+    int m = 0;
+    int64_t n = 0, r0 = 0, hs = 0;
+    if (valid) {
+      p = a.list ? a.list[base + idx] : (int32_t)(base + idx);
+      const int32_t ri = a.pair_read[p], hi = a.pair_hap[p];
+      if (ri >= 0 && ri < a.n_reads && hi >= 0 && hi < a.n_haps) {
+        r0 = a.read_off[ri];
+        m = (int)(a.read_off[ri + 1] - r0);
+        hs = hap_start(a.hap_off[hi], hi);
+        n = a.hap_off[hi + 1] - a.hap_off[hi];
+        if (m <= 0 || m > L * K || n <= 0) bad = true;
+      } else {
+        bad = true;
+      }
+      if (bad) {
+        m = 0;
+        n = 0;
+      }
+    }
+    const int npad = L * K - m;
+    // K0 * D(0, j), carried in I; the per-lane-exponent tier starts from K0 = 1
+    const T bnd = n > 0 ? (EXT ? (T)1 : Num<T>::K0) / (T)n : (T)0;
+
+    // ---- per-row constants and the emission table ---------------------------------------
+    // Per-lane-exponent tier: row r of every lane is stored with an extra factor 2^(kBias*r)
+    // (folded exactly into the row's emission, delta and I coefficients), which offsets the
+    // typical decay of the forward values down the rows so one exponent covers the lane.
+    constexpr int kBias = EXT ? 2 : 0;
+    T ap[K], dl[K], zt[K], ei[K], M[K], I[K], D[K];
+#pragma unroll
+    for (int r0v = 0; r0v < K; r0v += VW) {
+      T ev[kCodes][VW];
+#pragma unroll
+      for (int u = 0; u < VW; ++u) {
+        const int rr = r0v + u;
+        const int pos = t * K + rr - npad;  // 0-based read position; < 0: pad row
+        const T bias = rr ? (T)(1 << kBias) : (T)1;
+        M[rr] = 0;
+        D[rr] = 0;
+        if (pos >= 0) {
+          T Q;
+          row_params<T>(a, r0 + pos, ap[rr], dl[rr], zt[rr], Q);
+          const int code = a.rcode[r0 + pos];
+          ei[rr] = pos == 0 ? (T)0 : eps * bias;
+          dl[rr] *= bias;
+          I[rr] = 0;
+          const T em = bias * (beta * ((T)1 - Q)), ex = bias * (beta * (Q / (T)3));
+#pragma unroll
+          for (int c = 0; c < kNull; ++c)
+            ev[c][u] = (c == code || c == kN || code == kN) ? em : ex;
+          ev[kNull][u] = 0;
+        } else {
+          ap[rr] = 0;
+          dl[rr] = 0;
+          zt[rr] = 0;
+          ei[rr] = bias;
+          I[rr] = bnd * (T)(1ll << (kBias * rr));
+#pragma unroll
+          for (int c = 0; c < kCodes; ++c) ev[c][u] = 0;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < kCodes; ++c) store_vec<T, VW>(tbl + c * CS + r0v, ev[c]);
+    }
+
+    // ---- wavefront ------------------------------------------------------------------------
+    int steps = n > 0 ? (int)n + L - 1 : 0;
+    steps = __reduce_max_sync(FULL, steps);
+    WfState<T, K> st;
+    st.c = kNull;
+    st.Md = 0;
+    st.Sd = t == 0 ? bnd : (T)0;
+    st.acc = 0;
+    st.f = t == 0 ? (T)1 : Num<T>::exp2i(-kBias * (K - 1));
+    st.E = 0;
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+      st.M[r] = M[r];
+      st.I[r] = I[r];
+      st.D[r] = D[r];
+    }
+    const uint4 null16 = make_uint4(0x05050505u, 0x05050505u, 0x05050505u, 0x05050505u);
+    // Ramp: the first steps carry the wavefront into every lane; in the per-lane-exponent
+    // tier each lane renormalises after every one of them, so a lane adopts its exponent from
+    // the values about to reach it rather than from its empty initial state.
+    const int ramp = steps < ((L + 15) & ~15) ? steps : ((L + 15) & ~15);
+    // The result is taken at the first renormalisation point after the pair's last column:
+    // later steps (other pairs of the warp still running) only rescale it by powers of two,
+    // which would change the rounding of log10 and make results depend on the packing.
+    const int fin = n > 0 ? (int)n + L - 1 : 0;
+    T Sfin = 0;
+    int Efin = 0;
+    bool done = false;
+    uint4 hv = null16;
+    for (int s = 0; s < ramp; ++s) {
+      if ((s & 15) == 0) hv = (t == 0 && s < n) ? *reinterpret_cast<const uint4 *>(a.hcode + hs + s)
+                                                : null16;
+      const int q = (s >> 2) & 3;
+      const uint32_t w = q == 0 ? hv.x : (q == 1 ? hv.y : (q == 2 ? hv.z : hv.w));
+      T in3[3];
+      wf_step<T, L, K, EXT>(st, (w >> (8 * (s & 3))) & 0xff, t, bnd, eps, tbl, ap, dl, zt, ei,
+                            in3);
+      if (!done && s + 1 >= fin) {
+        Sfin = st.acc;
+        Efin = st.E;
+        done = true;
+      }
+      if constexpr (EXT) wf_rescale<T, L, K, kBias>(st, t);
+    }
+    for (int s0 = ramp; s0 < steps; s0 += 16) {
+      hv = (t == 0 && s0 < n) ? *reinterpret_cast<const uint4 *>(a.hcode + hs + s0) : null16;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const uint32_t w = u < 4 ? hv.x : (u < 8 ? hv.y : (u < 12 ? hv.z : hv.w));
+        T in3[3];
+        wf_step<T, L, K, EXT>(st, (w >> (8 * (u & 3))) & 0xff, t, bnd, eps, tbl, ap, dl, zt, ei,
+                              in3);
+      }
+      if (!done && s0 + 16 >= fin) {
+        Sfin = st.acc;
+        Efin = st.E;
+        done = true;
+      }
+      if constexpr (EXT) wf_rescale<T, L, K, kBias>(st, t);
+    }
+    if (!done) {
+      Sfin = st.acc;
+      Efin = st.E;
+    }
+    const T acc = Sfin;
+    const int E = Efin;
+
+    // ---- result: the last lane holds row m ------------------------------------------------
+    if (valid && t == L - 1) {
+      if (bad) {
+        a.out[p] = __longlong_as_double(0x7ff8000000000000ll);
+        a.flags[p] = PHMM_FLAG_INVALID;
+      } else {
+        constexpr double LOG10_2 = 0.301029995663981195213738894724493027;
+        const double S = (double)acc;
+        const bool finite = S < 1.7976931348623157e308;
+        bool ok;
+        double lg;
+        if constexpr (EXT) {
+          ok = S > 0.0 && finite;
+          lg = log10(S) + (double)(E - kBias * (K - 1)) * LOG10_2;
+        } else if constexpr (sizeof(T) == 4) {
+          ok = acc >= kMinAccepted32 && finite;
+          lg = log10(S) - 120.0 * LOG10_2;
+        } else {
+          ok = S >= kMinAccepted64 && finite;
+          lg = log10(S) - 1020.0 * LOG10_2;
+        }
+        if (ok || !a.rescue) {
+          a.out[p] = lg;
+          a.flags[p] = (uint8_t)(sizeof(T) == 4 ? PHMM_FLAG_FP32 : PHMM_FLAG_RESCUED64) |
+                       (uint8_t)(EXT ? PHMM_FLAG_EXTENDED : 0);
+        } else {
+          const int b = bin64_of_m(m);
+          const int pos = atomicAdd(&a.rescue_count[b], 1);
+          a.rescue_list[b][pos] = p;
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int L, int K>
+inline size_t wf_smem(int block) {
+  return (size_t)(block / 32) * TableGeom<T, K>::warp_bytes;
+}
+
+}  // namespace phmm

@@ -1,0 +1,263 @@
+"""Thin Python binding of libphmm (include/phmm.h): argument marshalling only.
+
+Every step of the Pair-HMM path runs in the library's CUDA kernels; PyTorch provides device
+memory and the current stream.  There is no CPU fallback: if the shared library cannot be
+loaded, importing the binding's entry points raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+PHMM_OK, PHMM_EINVAL, PHMM_ETOOLONG, PHMM_ENOMEM, PHMM_ECUDA, PHMM_ESTATE = 0, -1, -2, -3, -4, -5
+PHMM_MAX_READ_LEN = 512
+FLAG_FP32, FLAG_RESCUED64, FLAG_EXTENDED, FLAG_INVALID = 1, 2, 4, 8
+QUAL_U8, QUAL_F32 = 0, 1
+FIRST_PLAIN32, FIRST_EXT32 = 0, 1
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libphmm.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class PhmmError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        msg = lib().phmm_status_str(status).decode() if _lib is not None else str(status)
+        if status == PHMM_ECUDA and _lib is not None:
+            msg += f" (cudaError {_lib.phmm_last_cuda_error()})"
+        super().__init__(f"{what}: {msg} [{status}]")
+
+
+class Batch(ctypes.Structure):
+    _fields_ = [
+        ("n_reads", ctypes.c_int64), ("n_haps", ctypes.c_int64), ("n_pairs", ctypes.c_int64),
+        ("read_bases", ctypes.c_void_p), ("base_q", ctypes.c_void_p),
+        ("ins_q", ctypes.c_void_p), ("del_q", ctypes.c_void_p),
+        ("qual_dtype", ctypes.c_int32), ("alpha_mode", ctypes.c_int32),
+        ("read_off", ctypes.c_void_p), ("hap_bases", ctypes.c_void_p),
+        ("hap_off", ctypes.c_void_p), ("pair_read", ctypes.c_void_p),
+        ("pair_hap", ctypes.c_void_p), ("gcp", ctypes.c_double),
+    ]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("first_line", ctypes.c_int32), ("rescue", ctypes.c_int32),
+        ("binning", ctypes.c_int32), ("lanes", ctypes.c_int32), ("rows", ctypes.c_int32),
+        ("persistent", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+        ("warps_per_block", ctypes.c_int32),
+        ("bin_rows", ctypes.c_int32 * (PHMM_MAX_READ_LEN // 4 + 1)),
+        ("bin_table_valid", ctypes.c_int32),
+    ]
+
+
+def lib():
+    """Load libphmm.so (build it first with __graft_entry__.build() or _build.build())."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise ImportError(f"libphmm.so not built at {_LIB_PATH}; run the package build")
+            L = ctypes.CDLL(_LIB_PATH)
+            vp, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)
+            L.phmm_options_default.argtypes = [ctypes.POINTER(Options)]
+            L.phmm_options_default.restype = None
+            L.phmm_plan_create.argtypes = [ctypes.POINTER(Batch), ctypes.POINTER(Options), vp,
+                                           ctypes.POINTER(vp)]
+            L.phmm_plan_create.restype = ctypes.c_int
+            L.phmm_workspace_bytes.argtypes = [vp]
+            L.phmm_workspace_bytes.restype = ctypes.c_size_t
+            L.phmm_plan_info.argtypes = [vp, i64p, i64p, i64p]
+            L.phmm_plan_info.restype = ctypes.c_int
+            L.phmm_forward.argtypes = [vp, vp, ctypes.c_size_t, vp, vp, vp]
+            L.phmm_forward.restype = ctypes.c_int
+            L.phmm_backward.argtypes = [vp, vp, ctypes.c_size_t, vp, vp, vp, vp, vp, vp]
+            L.phmm_backward.restype = ctypes.c_int
+            L.phmm_plan_destroy.argtypes = [vp]
+            L.phmm_plan_destroy.restype = None
+            L.phmm_status_str.argtypes = [ctypes.c_int]
+            L.phmm_status_str.restype = ctypes.c_char_p
+            L.phmm_last_cuda_error.argtypes = []
+            L.phmm_last_cuda_error.restype = ctypes.c_int
+            L.phmm_plan_launch_count.argtypes = [vp, ctypes.c_int]
+            L.phmm_plan_launch_count.restype = ctypes.c_int
+            L.phmm_plan_wavefront_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float),
+                                                 ctypes.POINTER(ctypes.c_float)]
+            L.phmm_plan_wavefront_ms.restype = ctypes.c_int
+            L.phmm_probe_pipe.argtypes = [ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]
+            L.phmm_probe_pipe.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def options(**kw) -> Options:
+    """Library defaults (phmm_options_default) with keyword overrides; `bin_rows` may be a
+    sequence of group ids per 4-row read-length bucket (sets bin_table_valid)."""
+    o = Options()
+    lib().phmm_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "bin_rows":
+            for i, x in enumerate(v):
+                o.bin_rows[i] = int(x)
+            o.bin_table_valid = 1
+        else:
+            setattr(o, k, int(v))
+    return o
+
+
+def _stream(stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class DeviceBatch:
+    """A host batch (dict of numpy arrays, see synth.py) copied to device tensors."""
+
+    def __init__(self, batch, device="cuda", non_blocking=False):
+        import torch
+        self.host = batch
+        qd = np.asarray(batch["base_q"]).dtype
+        self.qual_dtype = QUAL_F32 if qd == np.float32 else QUAL_U8
+        qt = torch.float32 if self.qual_dtype == QUAL_F32 else torch.uint8
+
+        def dev(a, dt):
+            t = torch.from_numpy(np.ascontiguousarray(a))
+            if non_blocking:
+                t = t.pin_memory()
+            return t.to(device=device, dtype=dt, non_blocking=non_blocking)
+
+        self.read_bases = dev(batch["read_bases"], torch.uint8)
+        self.base_q = dev(batch["base_q"], qt)
+        self.ins_q = dev(batch["ins_q"], qt)
+        self.del_q = dev(batch["del_q"], qt)
+        self.read_off = dev(batch["read_off"], torch.int64)
+        self.hap_bases = dev(batch["hap_bases"], torch.uint8)
+        self.hap_off = dev(batch["hap_off"], torch.int64)
+        self.pair_read = dev(batch["pair_read"], torch.int32)
+        self.pair_hap = dev(batch["pair_hap"], torch.int32)
+        self.gcp = float(batch["gcp"])
+        self.alpha_mode = int(batch.get("alpha_mode", 0))
+
+    @property
+    def n_pairs(self):
+        return int(self.pair_read.numel())
+
+    def struct(self) -> Batch:
+        b = Batch()
+        b.n_reads = self.read_off.numel() - 1
+        b.n_haps = self.hap_off.numel() - 1
+        b.n_pairs = self.pair_read.numel()
+        b.read_bases = self.read_bases.data_ptr()
+        b.base_q = self.base_q.data_ptr()
+        b.ins_q = self.ins_q.data_ptr()
+        b.del_q = self.del_q.data_ptr()
+        b.qual_dtype = self.qual_dtype
+        b.alpha_mode = self.alpha_mode
+        b.read_off = self.read_off.data_ptr()
+        b.hap_bases = self.hap_bases.data_ptr()
+        b.hap_off = self.hap_off.data_ptr()
+        b.pair_read = self.pair_read.data_ptr() if b.n_pairs else None
+        b.pair_hap = self.pair_hap.data_ptr() if b.n_pairs else None
+        b.gcp = self.gcp
+        return b
+
+
+class Plan:
+    """phmm_plan_create + a torch-allocated workspace; forward/backward on torch tensors."""
+
+    def __init__(self, dbatch: DeviceBatch, opts: Options | None = None, stream=None):
+        import torch
+        self.dbatch = dbatch
+        self._b = dbatch.struct()
+        self.opts = opts if opts is not None else options()
+        h = ctypes.c_void_p()
+        rc = lib().phmm_plan_create(ctypes.byref(self._b), ctypes.byref(self.opts),
+                                    _stream(stream), ctypes.byref(h))
+        if rc != PHMM_OK:
+            raise PhmmError(rc, "phmm_plan_create")
+        self.handle = h
+        self.ws_bytes = int(lib().phmm_workspace_bytes(h))
+        dev = dbatch.read_bases.device
+        self.workspace = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=dev)
+        off = (-self.workspace.data_ptr()) % 256
+        self._ws_ptr = self.workspace.data_ptr() + off
+        sm, sn, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        lib().phmm_plan_info(h, ctypes.byref(sm), ctypes.byref(sn), ctypes.byref(c))
+        self.sum_m, self.sum_n, self.cells = sm.value, sn.value, c.value
+
+    def forward(self, out=None, flags=None, stream=None):
+        import torch
+        P = self.dbatch.n_pairs
+        dev = self.dbatch.read_bases.device
+        if out is None:
+            out = torch.empty(P, dtype=torch.float64, device=dev)
+        if flags is None:
+            flags = torch.empty(P, dtype=torch.uint8, device=dev)
+        rc = lib().phmm_forward(self.handle, ctypes.c_void_p(self._ws_ptr), self.ws_bytes,
+                                ctypes.c_void_p(out.data_ptr() if P else 0),
+                                ctypes.c_void_p(flags.data_ptr() if P else 0), _stream(stream))
+        if rc != PHMM_OK:
+            raise PhmmError(rc, "phmm_forward")
+        return out, flags
+
+    def backward(self, dL, stream=None):
+        import torch
+        dev = self.dbatch.read_bases.device
+        tot = max(self.sum_m, 1)
+        dbq = torch.empty(tot, dtype=torch.float32, device=dev)
+        diq = torch.empty(tot, dtype=torch.float32, device=dev)
+        ddq = torch.empty(tot, dtype=torch.float32, device=dev)
+        dgcp = torch.empty(1, dtype=torch.float64, device=dev)
+        dL = dL.to(device=dev, dtype=torch.float64).contiguous()
+        rc = lib().phmm_backward(self.handle, ctypes.c_void_p(self._ws_ptr), self.ws_bytes,
+                                 ctypes.c_void_p(dL.data_ptr()), ctypes.c_void_p(dbq.data_ptr()),
+                                 ctypes.c_void_p(diq.data_ptr()), ctypes.c_void_p(ddq.data_ptr()),
+                                 ctypes.c_void_p(dgcp.data_ptr()), _stream(stream))
+        if rc != PHMM_OK:
+            raise PhmmError(rc, "phmm_backward")
+        return dbq[: self.sum_m], diq[: self.sum_m], ddq[: self.sum_m], dgcp
+
+    def launch_count(self, which=0):
+        return int(lib().phmm_plan_launch_count(self.handle, which))
+
+    def wavefront_ms(self):
+        a, r = ctypes.c_float(), ctypes.c_float()
+        lib().phmm_plan_wavefront_ms(self.handle, ctypes.byref(a), ctypes.byref(r))
+        return a.value, r.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().phmm_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def forward(batch, opts: Options | None = None, device="cuda"):
+    """log10 P(read | haplotype) and flags for every pair of a host or device batch."""
+    db = batch if isinstance(batch, DeviceBatch) else DeviceBatch(batch, device)
+    plan = Plan(db, opts)
+    out, flags = plan.forward()
+    return out, flags
+
+
+def probe_pipe(kind: int, iters: int = 4000):
+    """Lane operations per second of FFMA (0), packed f32x2 FMA (1) or DFMA (2)."""
+    r, ms = ctypes.c_double(), ctypes.c_double()
+    rc = lib().phmm_probe_pipe(kind, iters, ctypes.byref(r), ctypes.byref(ms))
+    if rc != PHMM_OK:
+        raise PhmmError(rc, "phmm_probe_pipe")
+    return r.value, ms.value

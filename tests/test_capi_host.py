@@ -1,0 +1,72 @@
+"""Host-side checks of the C ABI (no GPU): the library builds, loads and exports every entry
+point include/phmm.h declares; argument checks that need no device answer correctly."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2411_11547_gb300 import _build, phmm
+    _build.build()
+    return phmm.lib()
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(phmm_\w+)\s*\(", src, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("phmm_plan_create", "phmm_forward", "phmm_backward", "phmm_workspace_bytes",
+                 "phmm_plan_destroy", "phmm_status_str"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    for code in (0, -1, -2, -3, -4, -5):
+        assert lib.phmm_status_str(code)
+    assert lib.phmm_status_str(-99) == b"unknown status"
+
+
+def test_options_default(lib):
+    from paper_2411_11547_gb300 import phmm
+    o = phmm.options()
+    assert o.first_line == phmm.FIRST_EXT32 and o.rescue == 1 and o.binning == 1
+    assert o.use_graph == 1 and o.persistent == 1 and o.bin_table_valid == 0
+
+
+def test_plan_create_rejects_bad_arguments_on_host(lib):
+    from paper_2411_11547_gb300 import phmm
+    h = ctypes.c_void_p()
+    assert lib.phmm_plan_create(None, None, None, ctypes.byref(h)) == phmm.PHMM_EINVAL
+    b = phmm.Batch()  # n_reads = 0
+    assert lib.phmm_plan_create(ctypes.byref(b), None, None, ctypes.byref(h)) == phmm.PHMM_EINVAL
+    b.n_reads, b.n_haps, b.n_pairs = 1, 1, 1
+    b.gcp = 10.0  # NULL data pointers
+    assert lib.phmm_plan_create(ctypes.byref(b), None, None, ctypes.byref(h)) == phmm.PHMM_EINVAL
+    assert not h.value
+
+
+def test_forward_rejects_null_plan(lib):
+    from paper_2411_11547_gb300 import phmm
+    assert lib.phmm_forward(None, None, 0, None, None, None) == phmm.PHMM_EINVAL
+    assert lib.phmm_backward(None, None, 0, None, None, None, None, None, None) == phmm.PHMM_EINVAL
+    assert lib.phmm_workspace_bytes(None) == 0

@@ -1,0 +1,119 @@
+"""GPU adjoint vs the FP64 oracle adjoint, through the C ABI.
+
+Bar: gradients within 1e-3 relative.  An element whose reference is tiny compared with the
+rest of its array is compared with an absolute floor of 1e-5 x max|reference| of that array
+(FP32 sums of posterior-scale terms carry an absolute, not relative, rounding error).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2411_11547_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+RTOL, FLOOR = 1e-3, 1e-5
+
+
+@pytest.fixture(scope="module")
+def phmm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2411_11547_gb300 import _build, phmm as ph
+    _build.build()
+    ph.lib()
+    return ph
+
+
+def grad_close(got, want, name):
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    assert np.all(np.isfinite(got)), f"{name}: non-finite"
+    tol = RTOL * np.abs(want) + FLOOR * max(np.abs(want).max(), 1e-300)
+    bad = np.abs(got - want) > tol
+    if bad.any():
+        i = np.argmax(np.abs(got - want) - tol)
+        raise AssertionError(f"{name}: {bad.sum()} of {bad.size} outside tolerance; worst at {i}:"
+                             f" got {got[i]:.6g} want {want[i]:.6g}")
+
+
+def run_grad(ph, batch, dy, **opt):
+    import torch
+    plan = ph.Plan(ph.DeviceBatch(batch), ph.options(**opt))
+    out, flags = plan.forward()
+    gb, gi, gd, gg = plan.backward(torch.as_tensor(dy, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    return (out.cpu().numpy(), gb.cpu().numpy(), gi.cpu().numpy(), gd.cpu().numpy(),
+            float(gg.cpu().numpy()[0]), plan)
+
+
+def check_against_oracle(ph, b, dy, **opt):
+    y, gb, gi, gd, gg, _ = run_grad(ph, b, dy, **opt)
+    wy, wb, wi, wd, wg = oracle.backward_batch(b, dy)
+    grad_close(gb, wb, "d/dbq")
+    grad_close(gi, wi, "d/diq")
+    grad_close(gd, wd, "d/ddq")
+    assert abs(gg - wg) <= RTOL * abs(wg) + 1e-9, (gg, wg)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_random_pairs(phmm, seed):
+    b = synth.random_pairs(60 + seed, 150, (1, 300), (1, 500), alphabet=b"ACGTN", related=0.5,
+                           qual_dtype=np.float32)
+    dy = np.random.default_rng(seed).uniform(-1.5, 2.0, len(b["pair_read"]))
+    check_against_oracle(phmm, b, dy)
+
+
+def test_shared_reads_all_vs_all(phmm):
+    # C3-shaped: regions of 16 haplotypes x 64 reads (here 3 regions), reads shared by pairs
+    b = synth.c3_grad(pairs=16 * 64 * 2 + 16 * 5)
+    dy = np.ones(len(b["pair_read"]))
+    check_against_oracle(phmm, b, dy)
+
+
+def test_alpha_mode_and_u8_quals(phmm):
+    b = synth.random_pairs(77, 80, (5, 200), (5, 300), related=0.6)
+    for am in (0, 1):
+        bb = dict(b, alpha_mode=am)
+        dy = np.linspace(-1, 1, len(b["pair_read"]))
+        check_against_oracle(phmm, bb, dy)
+
+
+def test_every_backward_group(phmm):
+    # read lengths that land in each backward group (rows per lane 4/8/12/16)
+    rng = np.random.default_rng(5)
+    regs = []
+    for m in [3, 16, 17, 32, 40, 48, 60, 64, 90, 96, 120, 128, 150, 192, 200, 256, 300, 384, 400,
+              512]:
+        n = int(rng.integers(max(m, 20), m + 200))
+        hap = synth.ACGT[rng.integers(0, 4, n)]
+        read = hap[:m].copy()
+        regs.append(([hap], [read], [rng.integers(10, 41, m)], [rng.integers(30, 46, m)],
+                     [rng.integers(30, 46, m)]))
+        regs.append(([synth.ACGT[rng.integers(0, 4, n)]], [read], [rng.integers(10, 41, m)],
+                     [rng.integers(30, 46, m)], [rng.integers(30, 46, m)]))
+    b = synth._assemble(regs, 10.0, "groups", qual_dtype=np.float32)
+    dy = np.ones(len(b["pair_read"]))
+    check_against_oracle(phmm, b, dy)
+
+
+def test_backward_requires_forward(phmm):
+    import torch
+    b = synth.random_pairs(1, 4, (5, 10), (5, 10))
+    plan = phmm.Plan(phmm.DeviceBatch(b))
+    with pytest.raises(phmm.PhmmError) as e:
+        plan.backward(torch.ones(4, dtype=torch.float64, device="cuda"))
+    assert e.value.status == phmm.PHMM_ESTATE
+
+
+def test_backward_deterministic(phmm):
+    import torch
+    b = synth.c1_batched(regions=6)
+    b = dict(b, base_q=b["base_q"].astype(np.float32), ins_q=b["ins_q"].astype(np.float32),
+             del_q=b["del_q"].astype(np.float32))
+    dy = np.random.default_rng(2).normal(size=len(b["pair_read"]))
+    r1 = run_grad(phmm, b, dy)
+    r2 = run_grad(phmm, b, dy)
+    for x, y in zip(r1[1:5], r2[1:5]):
+        assert np.array_equal(np.asarray(x), np.asarray(y))
