@@ -163,6 +163,21 @@ int phmm_plan_launch_count(const phmm_plan *plan, int which /* 0 fwd, 1 bwd */);
 int phmm_plan_wavefront_ms(phmm_plan *plan, float *ms_fp32, float *ms_rescue);
 
 /*
+ * Elapsed time of the latest phmm_backward's adjoint wavefront kernels (FP32 pass and its
+ * FP64 hand-off pass) and of its FP64 gradient reduction, from CUDA events on the launching
+ * stream; -1 before the work has finished.
+ */
+int phmm_plan_backward_ms(phmm_plan *plan, float *ms_adjoint, float *ms_reduce);
+
+/*
+ * Rescue statistics of the latest calls on this plan and workspace, copied to the host
+ * (waits for `stream`): counts[0] pairs the forward recomputed in FP64, counts[1] of those
+ * that went on to the per-lane-exponent FP64 kernel, counts[2] pairs whose adjoint was
+ * finished in FP64, counts[3] reserved (0).
+ */
+int phmm_plan_rescue_counts(phmm_plan *plan, const void *ws, void *stream, int64_t *counts);
+
+/*
  * Arithmetic-pipe probe (roofline denominators): lane multiply-adds per second sustained
  * by one kernel on the current device.  kind 0 = FP32 FFMA, 1 = packed fma.rn.f32x2
  * (counted as two lane operations), 2 = FP64 DFMA.  Allocates and frees a small buffer.

@@ -27,6 +27,7 @@
 // products are scaled by 2^(E_fwd + E_adj).  Per-pair partials are written in FP32 and
 // reduced per read in FP64 (grad_reduce.cu).
 #include <cstdint>
+#include <algorithm>
 #include <cstring>
 #include <vector>
 #include "phmm_internal.cuh"
@@ -67,34 +68,73 @@ struct BwdArgs {
   const int64_t *poff;     // partial-gradient offsets per pair
   float *part_bq, *part_iq, *part_dq;
   double *pair_dgcp;
-  float *scratch;          // per-warp slots
-  int64_t slot_floats;
+  void *scratch;           // per-warp slots (elements of the kernel's type)
+  int64_t slot_elems;
   int32_t nchk;            // checkpoint capacity per slot
+  int32_t rescue;          // 1: this is the FP64 pass (write NaN on failure)
+  int32_t *resc_list[kNumCfg64];  // FP32 pass: pairs handed to the FP64 pass
+  int32_t *resc_count;
+  int32_t *why;                   // [2]: hand-offs for the scale range / non-finite partials
 };
 
-// Record widths (floats, multiples of 4) of a checkpoint and of a recorded step.
-__host__ __device__ constexpr int ck_width(int K) { return 3 * K + 4; }
-__host__ __device__ constexpr int cb_width(int K) { return (3 * K + 6 + 3) & ~3; }
-
-// Records are stored as [record][float4 group][lane], so one warp-wide 128-bit access
-// covers 512 contiguous bytes.
-template <int W>
-__device__ __forceinline__ void rec_store(float *base, int lane, const float (&v)[W]) {
-#pragma unroll
-  for (int g = 0; g < W / 4; ++g)
-    reinterpret_cast<float4 *>(base)[g * 32 + lane] =
-        make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+// Record widths (elements, multiples of the 16-byte vector) of a checkpoint and of a
+// recorded step: K rows of M, I, D plus the boundary values.
+template <typename T>
+__host__ __device__ constexpr int vec_w() { return 16 / (int)sizeof(T); }
+template <typename T>
+__host__ __device__ constexpr int ck_width(int K) {
+  return (3 * K + 4 + vec_w<T>() - 1) / vec_w<T>() * vec_w<T>();
 }
-template <int W>
-__device__ __forceinline__ void rec_load(const float *base, int lane, float (&v)[W]) {
+template <typename T>
+__host__ __device__ constexpr int cb_width(int K) {
+  return (3 * K + 6 + vec_w<T>() - 1) / vec_w<T>() * vec_w<T>();
+}
+
+// Records are stored as [record][16-byte group][lane], so one warp-wide 128-bit access
+// covers 512 contiguous bytes.
+template <typename T, int W>
+__device__ __forceinline__ void rec_store(T *base, int lane, const T (&v)[W]) {
+  if constexpr (sizeof(T) == 4) {
 #pragma unroll
-  for (int g = 0; g < W / 4; ++g) {
-    const float4 x = reinterpret_cast<const float4 *>(base)[g * 32 + lane];
-    v[4 * g] = x.x;
-    v[4 * g + 1] = x.y;
-    v[4 * g + 2] = x.z;
-    v[4 * g + 3] = x.w;
+    for (int g = 0; g < W / 4; ++g)
+      reinterpret_cast<float4 *>(base)[g * 32 + lane] =
+          make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+  } else {
+#pragma unroll
+    for (int g = 0; g < W / 2; ++g)
+      reinterpret_cast<double2 *>(base)[g * 32 + lane] = make_double2(v[2 * g], v[2 * g + 1]);
   }
+}
+template <typename T, int W>
+__device__ __forceinline__ void rec_load(const T *base, int lane, T (&v)[W]) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int g = 0; g < W / 4; ++g) {
+      const float4 x = reinterpret_cast<const float4 *>(base)[g * 32 + lane];
+      v[4 * g] = x.x;
+      v[4 * g + 1] = x.y;
+      v[4 * g + 2] = x.z;
+      v[4 * g + 3] = x.w;
+    }
+  } else {
+#pragma unroll
+    for (int g = 0; g < W / 2; ++g) {
+      const double2 x = reinterpret_cast<const double2 *>(base)[g * 32 + lane];
+      v[2 * g] = x.x;
+      v[2 * g + 1] = x.y;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T int_bits(int e) {
+  if constexpr (sizeof(T) == 4) return __int_as_float(e);
+  else return __longlong_as_double((long long)e);
+}
+template <typename T>
+__device__ __forceinline__ int bits_int(T x) {
+  if constexpr (sizeof(T) == 4) return __float_as_int(x);
+  else return (int)__double_as_longlong(x);
 }
 
 __device__ __forceinline__ int hap_code_at(const uint8_t *hcode, int64_t hs, int64_t n,
@@ -102,28 +142,75 @@ __device__ __forceinline__ int hap_code_at(const uint8_t *hcode, int64_t hs, int
   return (j >= 1 && j <= n) ? (int)hcode[hs + j - 1] : kNull;
 }
 
-template <int L, int K>
+// Adjoint state of one lane.
+template <typename T, int K>
+struct AdjState {
+  T u[K];      // u(i, j+1) = beta lambda M^ of the lane's rows at the column to the right
+  T Db[K];     // D^(i, j+1)
+  T Itop;      // I^ of the lane's top row at its current column (read by the lane above)
+  T diagU;     // u of the lower lane's top row one column to the right (own scale)
+  T fB;        // 2^(E_low - E_own) and the row bias, for values from the lane below
+  T seed;      // 1/L in the stored scale of the last row (last lane only)
+  int EB;      // per-lane exponent of the adjoints
+  bool nz;     // the lane held a nonzero adjoint at the latest renormalisation
+};
+
+// Renormalise the adjoints of a lane by a power of two; a lane that holds only zeros takes
+// the exponent that makes the next values from the lane below arrive near 1.
+// `apply` selects the lanes that renormalise now (the exchange runs on every lane).
+template <typename T, int L, int K, int kBias>
+__device__ __forceinline__ void adj_rescale(AdjState<T, K> &as, int t, T S, int ES,
+                                            bool apply = true) {
+  constexpr unsigned FULL = 0xffffffffu;
+  T mx = fmax(as.Itop, as.diagU);
+#pragma unroll
+  for (int r = 0; r < K; ++r) mx = fmax(mx, fmax(as.u[r], as.Db[r]));
+  const bool zero = !(mx > (T)0);
+  if (apply) as.nz = !zero;
+  if (apply && !zero) {
+    const int En = as.EB + Num<T>::ilog2(mx);
+    const T sc = Num<T>::exp2i(as.EB - En);
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+      as.u[r] *= sc;
+      as.Db[r] *= sc;
+    }
+    as.Itop *= sc;
+    as.diagU *= sc;
+    as.EB = En;
+  }
+  const T xb = fmax(as.u[0], as.Itop);
+  const int Elow = __shfl_down_sync(FULL, as.EB, 1, L);
+  const T xbl = __shfl_down_sync(FULL, xb, 1, L);
+  if (apply && zero && t < L - 1)
+    as.EB = Elow - kBias * (K - 1) + (xbl > (T)0 ? Num<T>::ilog2(xbl) : 0);
+  as.fB = t < L - 1 ? Num<T>::exp2i(Elow - as.EB - kBias * (K - 1)) : (T)0;
+  as.seed = (t == L - 1 && S > (T)0) ? Num<T>::exp2i(-ES - as.EB) / S : (T)0;
+}
+
+template <typename T, int L, int K>
 __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
-  using T = float;
-  using G_ = TableGeom<float, K>;
-  constexpr int G = 32 / L, VW = 4, LS = G_::LS, CS = G_::CS;
+  using G_ = TableGeom<T, K>;
+  constexpr int G = 32 / L, VW = G_::VW, LS = G_::LS, CS = G_::CS;
   constexpr int kBias = 2;
-  constexpr int CKW = ck_width(K), CBW = cb_width(K);
+  constexpr int CKW = ck_width<T>(K), CBW = cb_width<T>(K);
+  constexpr int kHmax = sizeof(T) == 4 ? 200 : 1900;  // E_fwd + E_adj the split covers
   constexpr unsigned FULL = 0xffffffffu;
   const FwdArgs &fa = a.f;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int t = lane % L, sub = lane / L;
-  float *tblE = reinterpret_cast<float *>(smem_raw) + (size_t)warp * 2 * kCodes * CS + lane * LS;
-  float *tblW = tblE + kCodes * CS;
+  T *tblE = reinterpret_cast<T *>(smem_raw) + (size_t)warp * 2 * kCodes * CS + lane * LS;
+  T *tblW = tblE + kCodes * CS;
   const int wpb = blockDim.x >> 5;
-  float *slot = a.scratch + (size_t)(blockIdx.x * wpb + warp) * a.slot_floats;
-  float *ckb = slot;
-  float *cbb = slot + (size_t)a.nchk * 32 * CKW;
-  const T eps = fa.eps32, beta = fa.beta32;
+  T *slot = reinterpret_cast<T *>(a.scratch) + (size_t)(blockIdx.x * wpb + warp) * a.slot_elems;
+  T *ckb = slot;
+  T *cbb = slot + (size_t)a.nchk * 32 * CKW;
+  const T eps = sizeof(T) == 4 ? (T)fa.eps32 : (T)fa.eps64;
+  const T beta = sizeof(T) == 4 ? (T)fa.beta32 : (T)fa.beta64;
 
   const int64_t count = *fa.count_dev;
-  const int64_t base = *fa.offset_dev;
+  const int64_t base = fa.offset_dev ? *fa.offset_dev : 0;
   const int64_t nitems = (count + G - 1) / G;
 
   for (;;) {
@@ -175,7 +262,7 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
           row_params<T>(fa, r0 + pos, ap[rr], dl[rr], zt[rr], Q);
           const int code = fa.rcode[r0 + pos];
           ei[rr] = pos == 0 ? (T)0 : eps * bias;
-          cE[rr] = pos == 0 ? (T)0 : bias;
+          cE[rr] = ei[rr];
           dl[rr] *= bias;
           st.I[rr] = 0;
           const T em = bias * (beta * ((T)1 - Q)), ex = bias * (beta * (Q / (T)3));
@@ -205,10 +292,13 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
         store_vec<T, VW>(tblW + c * CS + rv, wv[c]);
       }
     }
-    // coefficients of the row just below the strip (the lower lane's row 0, unbiased)
+    // cE: the I -> I coefficient for the adjoint, equal to the forward's on real rows and 0
+    // on pad rows (whose adjoints are never needed; the forward's pass-through coefficient
+    // there would carry them up with growing stored magnitude).
+    // Coefficients of the row just below the strip (the lower lane's row 0, unbiased):
     const T apb = __shfl_down_sync(FULL, ap[0], 1, L);
     const T dlb = __shfl_down_sync(FULL, dl[0], 1, L);
-    const T eib = __shfl_down_sync(FULL, ei[0], 1, L);
+    const T eib = __shfl_down_sync(FULL, cE[0], 1, L);
 
     // ---- phase A: forward with checkpoints -------------------------------------------------
     int steps = n > 0 ? (int)n + L - 1 : 0;
@@ -229,7 +319,7 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
       const int b = q < ramp ? q : ramp + 16 * (q - ramp);
       const int len = q < ramp ? 1 : 16;
       {
-        float ck[CKW];
+        T ck[CKW];
 #pragma unroll
         for (int r = 0; r < K; ++r) {
           ck[r] = st.M[r];
@@ -239,8 +329,10 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
         ck[3 * K] = st.Md;
         ck[3 * K + 1] = st.Sd;
         ck[3 * K + 2] = st.f;
-        ck[3 * K + 3] = __int_as_float(st.E);
-        rec_store<CKW>(ckb + (size_t)q * 32 * CKW, lane, ck);
+        ck[3 * K + 3] = int_bits<T>(st.E);
+#pragma unroll
+        for (int k = 3 * K + 4; k < CKW; ++k) ck[k] = 0;
+        rec_store<T, CKW>(ckb + (size_t)q * 32 * CKW, lane, ck);
       }
       for (int u = 0; u < len; ++u) {
         const int s = b + u;  // 0-based step index
@@ -259,26 +351,37 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
       Sfin = st.acc;
       Efin = st.E;
     }
-    // L = S * 2^(Efin - kBias (K-1)), held by the last lane of the group
+    // L = S * 2^(ES - kBias (K-1)), held by the last lane of the group
     const T S = __shfl_sync(FULL, Sfin, sub * L + L - 1);
     const int ES = __shfl_sync(FULL, Efin, sub * L + L - 1);
-    const bool okS = S > (T)0 && S < (T)3.0e38f;
+    const bool okS = S > (T)0 && S < (sizeof(T) == 4 ? (T)3.0e38f : (T)1.7e308);
+    bool hard = !okS;
 
     // ---- phase B: adjoint, segment by segment from the right ------------------------------
-    int EB = -st.E;  // adjoint exponent tied to the forward's at the right edge
-    T u[K], Db[K], gA[K], gQ[K], gD[K], gZ[K];
+    AdjState<T, K> as;
 #pragma unroll
-    for (int r = 0; r < K; ++r) u[r] = Db[r] = gA[r] = gQ[r] = gD[r] = gZ[r] = 0;
-    T gS = 0, gE = 0, Itop = 0, diagU = 0;
-    T fB = Num<T>::exp2i(__shfl_down_sync(FULL, EB, 1, L) - EB - kBias * (K - 1));
-    T seed = okS ? Num<T>::exp2i(-ES - EB) / S : (T)0;
+    for (int r = 0; r < K; ++r) as.u[r] = as.Db[r] = 0;
+    as.Itop = as.diagU = 0;
+    as.EB = t == L - 1 ? -ES : 0;
+    as.fB = 0;
+    as.seed = 0;
+    as.nz = false;
+    adj_rescale<T, L, K, kBias>(as, t, okS ? S : (T)0, ES);
+    T gA[K], gQ[K], gD[K], gZ[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) gA[r] = gQ[r] = gD[r] = gZ[r] = 0;
+    T gS = 0, gE = 0, gEI = 0;
+    // the adjoint enters the pair's lanes one per step from its last column on: renormalise
+    // after every one of the first ramp_b such steps (a window set by the pair alone, so the
+    // result does not depend on which pairs share the warp), then at segment boundaries
+    const int ramp_b = 16 + ((L + 15) & ~15);
 
     for (int q = nq - 1; q >= 0; --q) {
       const int b = q < ramp ? q : ramp + 16 * (q - ramp);
       const int len = q < ramp ? 1 : 16;
       {
-        float ck[CKW];
-        rec_load<CKW>(ckb + (size_t)q * 32 * CKW, lane, ck);
+        T ck[CKW];
+        rec_load<T, CKW>(ckb + (size_t)q * 32 * CKW, lane, ck);
 #pragma unroll
         for (int r = 0; r < K; ++r) {
           st.M[r] = ck[r];
@@ -288,15 +391,14 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
         st.Md = ck[3 * K];
         st.Sd = ck[3 * K + 1];
         st.f = ck[3 * K + 2];
-        st.E = __float_as_int(ck[3 * K + 3]);
+        st.E = bits_int<T>(ck[3 * K + 3]);
       }
       st.c = hap_code_at(fa.hcode, hs, n, (int64_t)b - t);
-      const T g = Num<T>::exp2i(st.E + EB);
       // recompute the segment, recording each step's inputs
       for (int u2 = 0; u2 < len; ++u2) {
         const int s = b + u2;
         const int cu = (t == 0 && s < n) ? (int)fa.hcode[hs + s] : kNull;
-        float rec[CBW];
+        T rec[CBW];
 #pragma unroll
         for (int r = 0; r < K; ++r) {
           rec[r] = st.M[r];
@@ -310,11 +412,16 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
         rec[3 * K + 2] = in3[0];
         rec[3 * K + 3] = in3[1];
         rec[3 * K + 4] = in3[2];
-        rec[3 * K + 5] = __int_as_float(st.c);
+        rec[3 * K + 5] = int_bits<T>(st.c);
 #pragma unroll
         for (int k = 3 * K + 6; k < CBW; ++k) rec[k] = 0;
-        rec_store<CBW>(cbb + (size_t)u2 * 32 * CBW, lane, rec);
+        rec_store<T, CBW>(cbb + (size_t)u2 * 32 * CBW, lane, rec);
       }
+      const int EF = st.E;
+      T mxF = fmax(st.Md, st.Sd);
+#pragma unroll
+      for (int r = 0; r < K; ++r) mxF = fmax(mxF, fmax(st.M[r], fmax(st.I[r], st.D[r])));
+      const bool nzF = mxF > (T)0;
       T cM[K], cI[K];
 #pragma unroll
       for (int r = 0; r < K; ++r) {
@@ -323,121 +430,142 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
       }
       // reverse over the segment
       for (int u2 = len - 1; u2 >= 0; --u2) {
-        float rec[CBW];
-        rec_load<CBW>(cbb + (size_t)u2 * 32 * CBW, lane, rec);
+        T rec[CBW];
+        rec_load<T, CBW>(cbb + (size_t)u2 * 32 * CBW, lane, rec);
         const int64_t j = (int64_t)b + u2 + 1 - t;  // this lane's column at this step
-        const int c = __float_as_int(rec[3 * K + 5]);
+        const int c = bits_int<T>(rec[3 * K + 5]);
+        // posterior scale 2^(EF + EB), split between the adjoint and the forward factors
+        // h < -kHmax: every product is below 2^-150 of a posterior and flushes to 0, which
+        // is harmless; h > kHmax: forward and adjoint mass sit in disjoint cells of the lane
+        // and the split factors may overflow, so the pair is finished in FP64.
+        const int h = EF + as.EB;
+        if (h > kHmax && nzF && as.nz) hard = true;
+        // a lane-segment whose forward values are all zero (the wavefront has not reached it)
+        // contributes nothing; zero scales keep its adjoint tail from producing inf * 0
+        const T g1 = nzF ? Num<T>::exp2i(h >> 1) : (T)0;
+        const T g2 = nzF ? Num<T>::exp2i(h - (h >> 1)) : (T)0;
         T e[K], w[K];
         load_rows<T, K>(tblE + c * CS, e);
         load_rows<T, K>(tblW + c * CS, w);
-        T rU = __shfl_down_sync(FULL, u[0], 1, L);
-        T rI = __shfl_down_sync(FULL, Itop, 1, L);
+        T rU = __shfl_down_sync(FULL, as.u[0], 1, L);
+        T rI = __shfl_down_sync(FULL, as.Itop, 1, L);
         if (t == L - 1) {
           rU = 0;
           rI = 0;
         } else {
-          rU *= fB;
-          rI *= fB;
+          rU *= as.fB;
+          rI *= as.fB;
         }
-        const T ubK = diagU;
-        diagU = rU;
-        const T sd = (t == L - 1 && j >= 1 && j <= n) ? seed : (T)0;
+        const T ubK = as.diagU;
+        as.diagU = rU;
+        const T sd = (t == L - 1 && j >= 1 && j <= n) ? as.seed : (T)0;
         T ub = ubK, Ibl = rI;
-        const T Mds = rec[3 * K], Sds = rec[3 * K + 1], inM = rec[3 * K + 2],
-                inI = rec[3 * K + 3];
+        const T Mds = rec[3 * K] * g2, Sds = rec[3 * K + 1] * g2, inM = rec[3 * K + 2] * g2,
+                inI = rec[3 * K + 3] * g2;
 #pragma unroll
         for (int r = K - 1; r >= 0; --r) {
           const T apB = r == K - 1 ? apb : ap[r + 1];
           const T dlB = r == K - 1 ? dlb : dl[r + 1];
-          const T eiB = r == K - 1 ? eib : ei[r + 1];
+          const T eiB = r == K - 1 ? eib : cE[r + 1];
           const T add = r == K - 1 ? sd : (T)0;
-          const T Mb = apB * ub + dlB * Ibl + zt[r] * Db[r] + add;
+          const T Mb = apB * ub + dlB * Ibl + zt[r] * as.Db[r] + add;
           const T Ib = ub + eiB * Ibl + add;
-          const T Dn = ub + eps * Db[r];
+          const T Dn = ub + eps * as.Db[r];
           const T un = e[r] * Mb;
-          // partials (posterior scale: times g)
-          const T Mg = Mb * g, Ig = Ib * g, Dg = Dn * g, ag = un * g;
-          const T Mup = r ? rec[r - 1] : Mds;
-          const T Sup = r ? rec[K + r - 1] + rec[2 * K + r - 1] : Sds;
-          const T Mu = r ? cM[r - 1] : inM;
-          const T Iu = r ? cI[r - 1] : inI;
+          // partials: adjoint x 2^(h/2) times forward x 2^(h - h/2)
+          const T Mg = Mb * g1, Ig = Ib * g1, Dg = Dn * g1, ag = un * g1;
+          const T Mup = r ? rec[r - 1] * g2 : Mds;
+          const T Sup = r ? (rec[K + r - 1] + rec[2 * K + r - 1]) * g2 : Sds;
+          const T Mu = r ? cM[r - 1] * g2 : inM;
+          const T Iu = r ? cI[r - 1] * g2 : inI;
           gA[r] += ag * Mup;
           gS += ag * Sup;
           gQ[r] += (Mg * w[r]) * (ap[r] * Mup + Sup);
           gD[r] += Ig * Mu;
-          gE += (Ig * cE[r]) * Iu;
-          gZ[r] += Dg * rec[r];
-          gE += Dg * rec[2 * K + r];
-          ub = u[r];
-          u[r] = un;
-          Db[r] = Dn;
+          gEI += (Ig * cE[r]) * Iu;  // eps x the I -> I partial
+          gZ[r] += Dg * (rec[r] * g2);
+          gE += Dg * (rec[2 * K + r] * g2);
+          ub = as.u[r];
+          as.u[r] = un;
+          as.Db[r] = Dn;
           Ibl = Ib;
         }
-        Itop = Ibl;
+        as.Itop = Ibl;
 #pragma unroll
         for (int r = 0; r < K; ++r) {
           cM[r] = rec[r];
           cI[r] = rec[K + r];
         }
+        const int sf = b + u2 + 1;  // forward step just reversed
+        const bool apply = sf <= fin && (u2 == 0 || sf > fin - ramp_b);
+        adj_rescale<T, L, K, kBias>(as, t, okS ? S : (T)0, ES, apply);
       }
-      // renormalise the adjoint state of this lane
-      T mx = fmax(Itop, diagU);
-#pragma unroll
-      for (int r = 0; r < K; ++r) mx = fmax(mx, fmax(u[r], Db[r]));
-      if (mx > (T)0) {
-        const int En = EB + Num<T>::ilog2(mx);
-        const T sc = Num<T>::exp2i(EB - En);
-#pragma unroll
-        for (int r = 0; r < K; ++r) {
-          u[r] *= sc;
-          Db[r] *= sc;
-        }
-        Itop *= sc;
-        diagU *= sc;
-        EB = En;
-      }
-      fB = Num<T>::exp2i(__shfl_down_sync(FULL, EB, 1, L) - EB - kBias * (K - 1));
-      seed = okS ? Num<T>::exp2i(-ES - EB) / S : (T)0;
     }
 
     // ---- phase C: chain rule to the Phred inputs, per-pair partials ------------------------
-    T gSs = gS, gEs = gE;
+    T gSs = gS, gEs = gE + gEI / eps;
+    bool finite = true;  // over the real rows (pad rows' sums are never used)
+#pragma unroll
+    for (int r = 0; r < K; ++r)
+      if (t * K + r - npad >= 0)
+        finite = finite && fabs(gA[r]) < (T)1e30 && fabs(gQ[r]) < (T)1e30 &&
+                 fabs(gD[r]) < (T)1e30 && fabs(gZ[r]) < (T)1e30;  // false for NaN too
+    int hs_any = (hard || !finite) ? 1 : 0;
+    int why_h = hard ? 1 : 0, why_f = finite ? 0 : 1;
 #pragma unroll
     for (int o = 1; o < L; o <<= 1) {
       gSs += __shfl_xor_sync(FULL, gSs, o, L);
       gEs += __shfl_xor_sync(FULL, gEs, o, L);
+      hs_any |= __shfl_xor_sync(FULL, hs_any, o, L);
+      why_h |= __shfl_xor_sync(FULL, why_h, o, L);
+      why_f |= __shfl_xor_sync(FULL, why_f, o, L);
     }
+    const T dgcp_l = -(gEs - gSs / beta) * eps * (T)0.1;
+    if (!(fabs(dgcp_l) < (T)1e30)) hs_any = 1;
     if (valid && !bad) {
-      const double dy = a.dL[p];
-      const int64_t po = a.poff[p];
-      const T nanv = __int_as_float(0x7fc00000);
-#pragma unroll
-      for (int r = 0; r < K; ++r) {
-        const int pos = t * K + r - npad;
-        if (pos < 0) continue;
-        const RowParams v = fa.rp[r0 + pos];
-        const T del = v.y, zet = v.z, Q = v.w;
-        const T gAl = gA[r] / beta;
-        const T gDl = gD[r] * (r ? (T)(1 << kBias) : (T)1);
-        T db, di, dd;
-        if (fa.alpha_mode) {
-          const T iq = (T)qual_at(fa.iq, fa.qual_f32, r0 + pos);
-          const T dq = (T)qual_at(fa.dq, fa.qual_f32, r0 + pos);
-          const T pa = exp10f(-(iq + dq) * 0.1f);
-          di = -(gDl * del - gAl * pa) * 0.1f;
-          dd = -(gZ[r] * zet - gAl * pa) * 0.1f;
-        } else {
-          di = -(gDl - gAl) * del * 0.1f;
-          dd = -(gZ[r] - gAl) * zet * 0.1f;
+      const bool to_rescue = hs_any && !a.rescue;
+      if (to_rescue) {
+        if (t == 0) {
+          const int bin = bin64_of_m(m);
+          const int pos = atomicAdd(&a.resc_count[bin], 1);
+          a.resc_list[bin][pos] = p;
+          if (a.why) {
+            if (why_h) atomicAdd(&a.why[0], 1);
+            if (why_f) atomicAdd(&a.why[1], 1);
+          }
         }
-        db = -gQ[r] * Q * 0.1f;
-        a.part_bq[po + pos] = okS ? (float)(dy * db) : nanv;
-        a.part_iq[po + pos] = okS ? (float)(dy * di) : nanv;
-        a.part_dq[po + pos] = okS ? (float)(dy * dd) : nanv;
+      } else {
+        const double dy = a.dL[p];
+        const int64_t po = a.poff[p];
+        const bool ok = !hs_any;
+        const float nanv = __int_as_float(0x7fc00000);
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+          const int pos = t * K + r - npad;
+          if (pos < 0) continue;
+          T dum, del, zet, Q;
+          row_params<T>(fa, r0 + pos, dum, del, zet, Q);
+          const T gAl = gA[r] / beta;
+          const T gDl = gD[r] * (r ? (T)(1 << kBias) : (T)1);
+          T db, di, dd;
+          if (fa.alpha_mode) {
+            const T iq = (T)qual_at(fa.iq, fa.qual_f32, r0 + pos);
+            const T dq = (T)qual_at(fa.dq, fa.qual_f32, r0 + pos);
+            const T pa = sizeof(T) == 4 ? (T)exp10f((float)(-(iq + dq) * (T)0.1))
+                                        : (T)exp10(-(double)(iq + dq) / 10.0);
+            di = -(gDl * del - gAl * pa) * (T)0.1;
+            dd = -(gZ[r] * zet - gAl * pa) * (T)0.1;
+          } else {
+            di = -(gDl - gAl) * del * (T)0.1;
+            dd = -(gZ[r] - gAl) * zet * (T)0.1;
+          }
+          db = -gQ[r] * Q * (T)0.1;
+          a.part_bq[po + pos] = ok ? (float)(dy * (double)db) : nanv;
+          a.part_iq[po + pos] = ok ? (float)(dy * (double)di) : nanv;
+          a.part_dq[po + pos] = ok ? (float)(dy * (double)dd) : nanv;
+        }
+        if (t == 0) a.pair_dgcp[p] = ok ? dy * (double)dgcp_l : (double)nanv;
       }
-      if (t == 0)
-        a.pair_dgcp[p] =
-            okS ? -dy * ((double)gEs - (double)gSs / (double)beta) * (double)eps * 0.1 : (double)nanv;
     }
   }
 }
@@ -446,9 +574,11 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
 
 using BwdKernel = void (*)(const BwdArgs);
 
-static BwdKernel bwd_kernel(int L, int K) {
+// FP32 groups: lanes 4..32 x rows 4/8/12 (16 for the longest reads); FP64 hand-off groups:
+// 32 lanes x rows 4/8/16 (reads up to 128/256/512).
+static BwdKernel bwd_kernel32(int L, int K) {
 #define PHMM_BWD_CASE(LL, KK) \
-  if (L == LL && K == KK) return wf_backward<LL, KK>;
+  if (L == LL && K == KK) return wf_backward<float, LL, KK>;
   PHMM_BWD_CASE(4, 4) PHMM_BWD_CASE(4, 8) PHMM_BWD_CASE(4, 12)
   PHMM_BWD_CASE(8, 4) PHMM_BWD_CASE(8, 8) PHMM_BWD_CASE(8, 12)
   PHMM_BWD_CASE(16, 4) PHMM_BWD_CASE(16, 8) PHMM_BWD_CASE(16, 12)
@@ -456,13 +586,21 @@ static BwdKernel bwd_kernel(int L, int K) {
 #undef PHMM_BWD_CASE
   return nullptr;
 }
-
-static size_t bwd_smem(int K, int block) {
-  const int units = K * 4 / 16, LS = (units % 2 == 1) ? K : K + 4;
-  return (size_t)(block / 32) * 2 * kCodes * 32 * LS * 4;
+static BwdKernel bwd_kernel64(int K) {
+  switch (K) {
+    case 4: return wf_backward<double, 32, 4>;
+    case 8: return wf_backward<double, 32, 8>;
+    case 16: return wf_backward<double, 32, 16>;
+    default: return nullptr;
+  }
 }
 
-// Read length -> backward group (rows per lane <= 12 keeps the adjoint state in registers).
+static size_t bwd_smem(int K, int elem, int block) {
+  const int vw = 16 / elem, units = K * elem / 16, LS = (units % 2 == 1) ? K : K + vw;
+  return (size_t)(block / 32) * 2 * kCodes * 32 * LS * elem;
+}
+
+// Read length -> FP32 backward group (rows per lane <= 12 keeps the adjoint in registers).
 int bwd_default_cfg(int m) {
   struct Gp { int cap, L, K; };
   static const Gp order[] = {{16, 4, 4},   {32, 4, 8},    {48, 4, 12},  {64, 8, 8},
@@ -476,12 +614,11 @@ int bwd_default_cfg(int m) {
   return 3 * 5 + 3;
 }
 
-static int bwd_blocks_per_sm(int cfg, int block) {
-  BwdKernel k = bwd_kernel(cfg_lanes(cfg), cfg_rows(cfg));
+static int blocks_per_sm(BwdKernel k, size_t smem, int block) {
   if (!k) return 0;
   cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, bwd_smem(cfg_rows(cfg), block));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem);
   return nb < 1 ? 1 : nb;
 }
 
@@ -491,8 +628,10 @@ static int64_t bwd_nchk(int L, int64_t n_max) {
   return ramp + (steps + 15) / 16 + 2;
 }
 
-static int64_t bwd_slot_floats(int L, int K, int64_t n_max) {
-  return bwd_nchk(L, n_max) * 32 * ck_width(K) + 16 * 32 * cb_width(K);
+static int64_t slot_elems(int L, int K, int elem, int64_t n_max) {
+  const int vw = 16 / elem;
+  const int ckw = (3 * K + 4 + vw - 1) / vw * vw, cbw = (3 * K + 6 + vw - 1) / vw * vw;
+  return bwd_nchk(L, n_max) * 32 * ckw + 16 * 32 * cbw;
 }
 
 struct BwdLayout {
@@ -514,11 +653,20 @@ static BwdLayout bwd_layout(const phmm_plan *pl) {
   Lo.pdgcp = take(8 * (size_t)(b.n_pairs + 1));
   Lo.red = take(reduce_scratch_bytes_aligned(b.n_pairs, b.n_reads));
   size_t slots = 0;
+  const int64_t nmax = plan_n_max(pl);
   for (int cfg : plan_bwd_used(pl)) {
     const int L = cfg_lanes(cfg), K = cfg_rows(cfg);
-    const size_t nslot = (size_t)plan_sms(pl) * bwd_blocks_per_sm(cfg, block) * (block / 32);
-    const size_t bytes = nslot * 4 * (size_t)bwd_slot_floats(L, K, plan_n_max(pl));
-    if (bytes > slots) slots = bytes;
+    const size_t nslot = (size_t)plan_sms(pl) *
+                         blocks_per_sm(bwd_kernel32(L, K), bwd_smem(K, 4, block), block) *
+                         (block / 32);
+    slots = std::max(slots, nslot * 4 * (size_t)slot_elems(L, K, 4, nmax));
+  }
+  for (int c = 0; c < kNumCfg64; ++c) {
+    const int K = rows64(c);
+    const size_t nslot = (size_t)plan_sms(pl) *
+                         blocks_per_sm(bwd_kernel64(K), bwd_smem(K, 8, block), block) *
+                         (block / 32);
+    slots = std::max(slots, nslot * 8 * (size_t)slot_elems(32, K, 8, nmax));
   }
   Lo.slots = take(slots);
   Lo.total = o;
@@ -534,8 +682,10 @@ size_t bwd_workspace_bytes(const phmm_plan *pl) { return bwd_layout(pl).total; }
   } while (0)
 
 // returns a cudaError_t value (0 on success)
+// ev3: events recorded before the adjoint kernels, after them, and after the reduction.
 int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, float *diq,
-                     float *ddq, double *dgcp, cudaStream_t s, int *launches) {
+                     float *ddq, double *dgcp, cudaStream_t s, int *launches,
+                     cudaEvent_t *ev3) {
   const phmm_batch &b = plan_batch(pl);
   const phmm_options &o = plan_options(pl);
   const BwdLayout Lo = bwd_layout(pl);
@@ -549,10 +699,9 @@ int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, floa
   CKB(pair_offsets(b, red, &poff, s));
   *launches += 2;
   if (b.n_pairs > 0) {
-    // bin pairs by backward group, reusing the forward's sort buffers
+    // bin pairs by backward group, reusing the forward's sort buffers; zero the counters
     int32_t *counts = (int32_t *)(ws + plan_layout_bin(pl, 0));
-    CKB(cudaMemsetAsync(counts, 0, 4 * (size_t)kNumCfg32 * kNBuckets, s));
-    CKB(cudaMemsetAsync(ws + plan_layout_bin(pl, 7), 0, 4 * kNumCfg32, s));
+    CKB(cudaMemsetAsync(counts, 0, plan_layout_bin(pl, 9), s));
     CfgTable tab;
     const int *cm = plan_bwd_cfg_of_m(pl);
     for (int m = 0; m <= PHMM_MAX_READ_LEN; ++m) tab.cfg[m] = (int8_t)cm[m];
@@ -580,7 +729,6 @@ int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, floa
     f.alpha_mode = b.alpha_mode;
     f.n_reads = b.n_reads;
     f.n_haps = b.n_haps;
-    f.list = order;
     const double eps64 = plan_eps64(pl);
     f.eps32 = (float)eps64;
     f.beta32 = (float)(1.0 - eps64);
@@ -593,26 +741,61 @@ int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, floa
     a.part_iq = part_iq;
     a.part_dq = part_dq;
     a.pair_dgcp = pdg;
-    a.scratch = (float *)(bw + Lo.slots);
+    a.scratch = bw + Lo.slots;
+    int32_t *rlist = (int32_t *)(ws + plan_layout_bin(pl, 8));
+    int32_t *rcnt = counts + (size_t)kNumCfg32 * kNBuckets + kNumCfg32;  // in the zeroed region
+    int32_t *rctr = rcnt + kNumCfg64;
+    for (int k = 0; k < kNumCfg64; ++k)
+      a.resc_list[k] = rlist + (size_t)k * std::max<int64_t>(b.n_pairs, 1);
+    a.resc_count = rcnt;
+    a.why = (int32_t *)(ws + plan_layout_bin(pl, 10));
+    CKB(cudaMemsetAsync(a.why, 0, 16, s));
     const int block = 32 * o.warps_per_block;
+    const int64_t nmax = plan_n_max(pl);
+    CKB(cudaEventRecord(ev3[0], s));
     for (int cfg : plan_bwd_used(pl)) {
       const int L = cfg_lanes(cfg), K = cfg_rows(cfg);
       BwdArgs c = a;
+      c.f.list = order;
       c.f.offset_dev = grp_begin + cfg;
       c.f.count_dev = grp_count + cfg;
       c.f.counter = (int32_t *)(ws + plan_layout_bin(pl, 7)) + cfg;
-      c.nchk = (int32_t)bwd_nchk(L, plan_n_max(pl));
-      c.slot_floats = bwd_slot_floats(L, K, plan_n_max(pl));
-      const int grid = plan_sms(pl) * bwd_blocks_per_sm(cfg, block);
-      BwdKernel k = bwd_kernel(L, K);
+      c.nchk = (int32_t)bwd_nchk(L, nmax);
+      c.slot_elems = slot_elems(L, K, 4, nmax);
+      c.rescue = 0;
+      BwdKernel k = bwd_kernel32(L, K);
       if (!k) return (int)cudaErrorInvalidValue;
-      k<<<grid, block, bwd_smem(K, block), s>>>(c);
+      const size_t sm = bwd_smem(K, 4, block);
+      const int grid = plan_sms(pl) * blocks_per_sm(k, sm, block);
+      k<<<grid, block, sm, s>>>(c);
       CKB(cudaGetLastError());
       ++*launches;
     }
+    // FP64 pass over the pairs whose FP32 adjoint ran out of range
+    for (int k64 = 0; k64 < kNumCfg64; ++k64) {
+      const int K = rows64(k64);
+      BwdArgs c = a;
+      c.f.list = a.resc_list[k64];
+      c.f.offset_dev = nullptr;
+      c.f.count_dev = rcnt + k64;
+      c.f.counter = rctr + k64;
+      c.nchk = (int32_t)bwd_nchk(32, nmax);
+      c.slot_elems = slot_elems(32, K, 8, nmax);
+      c.rescue = 1;
+      BwdKernel kk = bwd_kernel64(K);
+      const size_t sm = bwd_smem(K, 8, block);
+      const int grid = plan_sms(pl) * blocks_per_sm(kk, sm, block);
+      kk<<<grid, block, sm, s>>>(c);
+      CKB(cudaGetLastError());
+      ++*launches;
+    }
+  } else {
+    CKB(cudaEventRecord(ev3[0], s));
   }
+  CKB(cudaEventRecord(ev3[1], s));
   CKB(reduce_gradients(b, red, part_bq, part_iq, part_dq, pdg, dbq, diq, ddq, dgcp, s,
                        launches));
+  CKB(cudaEventRecord(ev3[2], s));
   return 0;
 }
 

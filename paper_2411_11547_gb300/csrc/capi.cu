@@ -20,7 +20,8 @@ int launch_binning(const phmm_batch &b, const CfgTable &tab, int32_t *key, int32
                    int32_t *offsets, int32_t *cursor, int32_t *grp_begin, int32_t *grp_count,
                    int32_t *order, cudaStream_t s, int *launches);
 int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, float *diq,
-                     float *ddq, double *dgcp, cudaStream_t s, int *launches);
+                     float *ddq, double *dgcp, cudaStream_t s, int *launches,
+                     cudaEvent_t *ev3);
 size_t bwd_workspace_bytes(const phmm_plan *pl);
 int bwd_default_cfg(int m);
 
@@ -122,7 +123,7 @@ using namespace phmm;
 
 struct WsLayout {
   size_t rp, rcode, hcode, key, order, zero, zero_bytes, counts, ctr32, ctr64, ctrx, rcnt, xcnt,
-      offsets, cursor, grp_begin, grp_count, rlist, xlist, bwd, total;
+      offsets, cursor, grp_begin, grp_count, rlist, xlist, bwd, total, why;
 };
 
 struct phmm_plan {
@@ -140,7 +141,8 @@ struct phmm_plan {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t gexec = nullptr;
   void *g_ws = nullptr, *g_out = nullptr, *g_flags = nullptr;
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool bwd_timed = false;
   bool fwd_done = false;
   bool timed = false;  // the latest forward recorded the timing events
   int launches_fwd = 0, launches_bwd = 0;
@@ -178,6 +180,8 @@ static void make_layout(phmm_plan *pl) {
   o += 4 * kNumCfg64;
   L.xcnt = o;
   o += 4 * kNumCfg64;
+  L.why = o;  // adjoint hand-off reasons: scale range, non-finite partial, forward failed
+  o += 4 * 4;
   o = align256(o);
   L.zero_bytes = o - L.zero;
   L.offsets = take(4 * nkeys);
@@ -322,7 +326,7 @@ int phmm_plan_create(const phmm_batch *batch, const phmm_options *opt, void *str
   make_layout(pl);
   pl->L.total = pl->L.bwd + bwd_workspace_bytes(pl);
   cudaError_t ce = cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking);
-  for (int i = 0; i < 3 && ce == cudaSuccess; ++i) ce = cudaEventCreate(&pl->ev[i]);
+  for (int i = 0; i < 6 && ce == cudaSuccess; ++i) ce = cudaEventCreate(&pl->ev[i]);
   if (ce != cudaSuccess) {
     phmm_plan_destroy(pl);
     return cuda_fail(ce);
@@ -524,10 +528,12 @@ int phmm_backward(phmm_plan *pl, void *ws, size_t ws_bytes, const double *dL, fl
   if (!pl->fwd_done) return PHMM_ESTATE;
   (void)cudaGetLastError();
   int launches = 0;
+  pl->bwd_timed = false;
   int rc = bwd_enqueue_impl(pl, (char *)ws, dL, dbq, diq, ddq, dgcp, (cudaStream_t)stream,
-                            &launches);
+                            &launches, pl->ev + 3);
   pl->launches_bwd = launches;
   if (rc) return cuda_fail((cudaError_t)rc);
+  pl->bwd_timed = true;
   return PHMM_OK;
 }
 
@@ -545,6 +551,42 @@ int phmm_plan_wavefront_ms(phmm_plan *pl, float *ms_fp32, float *ms_rescue) {
   }
   if (ms_fp32) *ms_fp32 = a;
   if (ms_rescue) *ms_rescue = r;
+  return PHMM_OK;
+}
+
+int phmm_plan_rescue_counts(phmm_plan *pl, const void *ws, void *stream, int64_t *counts) {
+  if (!pl || !ws || !counts) return PHMM_EINVAL;
+  int32_t h[4 * kNumCfg64 + 4];
+  const char *w = (const char *)ws;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the forward's FP32->FP64 and FP64->extended counts, and the adjoint's FP32->FP64 count
+  // (kept in the slot after the forward's work counters, see the backward launch sequence)
+  CK(cudaMemcpyAsync(h, w + pl->L.rcnt, 4 * kNumCfg64, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h + kNumCfg64, w + pl->L.xcnt, 4 * kNumCfg64, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h + 2 * kNumCfg64, w + pl->L.ctr64, 4 * kNumCfg64, cudaMemcpyDeviceToHost,
+                     s));
+  CK(cudaMemcpyAsync(h + 3 * kNumCfg64, w + pl->L.why, 16, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  counts[0] = counts[1] = counts[2] = 0;
+  // counts[3]: hand-offs for the scale range, times 2^20 plus non-finite partials
+  counts[3] = ((int64_t)h[3 * kNumCfg64] << 20) + h[3 * kNumCfg64 + 1];
+  for (int k = 0; k < kNumCfg64; ++k) {
+    counts[0] += h[k];
+    counts[1] += h[kNumCfg64 + k];
+    counts[2] += h[2 * kNumCfg64 + k];
+  }
+  return PHMM_OK;
+}
+
+int phmm_plan_backward_ms(phmm_plan *pl, float *ms_adjoint, float *ms_reduce) {
+  if (!pl) return PHMM_EINVAL;
+  float a = -1.f, r = -1.f;
+  if (pl->bwd_timed && cudaEventQuery(pl->ev[5]) == cudaSuccess) {
+    if (cudaEventElapsedTime(&a, pl->ev[3], pl->ev[4]) != cudaSuccess) a = -1.f;
+    if (cudaEventElapsedTime(&r, pl->ev[4], pl->ev[5]) != cudaSuccess) r = -1.f;
+  }
+  if (ms_adjoint) *ms_adjoint = a;
+  if (ms_reduce) *ms_reduce = r;
   return PHMM_OK;
 }
 
@@ -566,11 +608,13 @@ int64_t plan_n_max(const phmm_plan *pl) { return pl->n_max; }
 int64_t plan_pair_rows(const phmm_plan *pl) { return pl->pair_rows; }
 const int *plan_bwd_cfg_of_m(const phmm_plan *pl) { return pl->bwd_cfg_of_m; }
 const std::vector<int> &plan_bwd_used(const phmm_plan *pl) { return pl->bwd_used; }
-// 0 counts, 1 key, 2 offsets, 3 cursor, 4 grp_begin, 5 grp_count, 6 order, 7 ctr32
+// 0 counts, 1 key, 2 offsets, 3 cursor, 4 grp_begin, 5 grp_count, 6 order, 7 ctr32,
+// 8 rescue lists, 9 (bytes the adjoint zeroes from counts on: up to the forward's rescue counts)
 size_t plan_layout_bin(const phmm_plan *pl, int which) {
   const WsLayout &L = pl->L;
-  const size_t v[8] = {L.counts, L.key, L.offsets, L.cursor, L.grp_begin, L.grp_count, L.order,
-                       L.ctr32};
+  const size_t v[11] = {L.counts,    L.key,   L.offsets, L.cursor,          L.grp_begin,
+                        L.grp_count, L.order, L.ctr32,   L.rlist,           L.rcnt - L.counts,
+                        L.why};
   return v[which];
 }
 }  // namespace phmm

@@ -89,6 +89,11 @@ def lib():
             L.phmm_plan_wavefront_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float),
                                                  ctypes.POINTER(ctypes.c_float)]
             L.phmm_plan_wavefront_ms.restype = ctypes.c_int
+            L.phmm_plan_backward_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float),
+                                                ctypes.POINTER(ctypes.c_float)]
+            L.phmm_plan_backward_ms.restype = ctypes.c_int
+            L.phmm_plan_rescue_counts.argtypes = [vp, vp, vp, i64p]
+            L.phmm_plan_rescue_counts.restype = ctypes.c_int
             L.phmm_probe_pipe.argtypes = [ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]
@@ -233,6 +238,20 @@ class Plan:
         a, r = ctypes.c_float(), ctypes.c_float()
         lib().phmm_plan_wavefront_ms(self.handle, ctypes.byref(a), ctypes.byref(r))
         return a.value, r.value
+
+    def backward_ms(self):
+        a, r = ctypes.c_float(), ctypes.c_float()
+        lib().phmm_plan_backward_ms(self.handle, ctypes.byref(a), ctypes.byref(r))
+        return a.value, r.value
+
+    def rescue_counts(self, stream=None):
+        """(forward FP64 rescues, of which extended, adjoint FP64 hand-offs) of the last calls."""
+        c = (ctypes.c_int64 * 4)()
+        rc = lib().phmm_plan_rescue_counts(self.handle, ctypes.c_void_p(self._ws_ptr),
+                                           _stream(stream), c)
+        if rc != PHMM_OK:
+            raise PhmmError(rc, "phmm_plan_rescue_counts")
+        return int(c[0]), int(c[1]), int(c[2]), int(c[3]) >> 20, int(c[3]) & 0xfffff
 
     def close(self):
         if getattr(self, "handle", None):

@@ -211,17 +211,86 @@ def _log_uniform_int(rng, lo, hi, size):
     return np.floor(np.exp(rng.uniform(np.log(lo), np.log(hi + 1), size=size))).astype(np.int64)
 
 
+def _bulk(rng, hap_len, hap_region, read_len, read_region, n_regions, bq, iq, dq, gcp, name,
+          qual_dtype=np.uint8):
+    """Vectorised batch of many regions (same read model as _sample_reads): haplotype and
+    read lengths and region ids are given; bases, sources, offsets and errors are drawn here.
+    Pairs are all-vs-all within each region."""
+    H, R = len(hap_len), len(read_len)
+    hap_off = np.concatenate([[0], np.cumsum(hap_len)]).astype(np.int64)
+    hap_bases = ACGT[rng.integers(0, 4, size=int(hap_off[-1]))]
+    # source haplotype: uniform among the region's haplotypes at least as long as the read
+    order = np.argsort(hap_region, kind="stable")
+    reg_first = np.searchsorted(hap_region[order], np.arange(n_regions))
+    reg_count = np.bincount(hap_region, minlength=n_regions)
+    maxh = int(reg_count.max())
+    cand = np.full((R, maxh), -1, dtype=np.int64)
+    for k in range(maxh):
+        has = k < reg_count[read_region]
+        h = order[np.minimum(reg_first[read_region] + k, H - 1)]
+        ok = has & (hap_len[h] >= read_len)
+        cand[:, k] = np.where(ok, h, -1)
+    n_ok = (cand >= 0).sum(axis=1)
+    assert np.all(n_ok > 0), "every read needs a haplotype at least as long"
+    pick = np.floor(rng.random(R) * n_ok).astype(np.int64)
+    srt = np.sort(np.where(cand >= 0, cand, np.iinfo(np.int64).max), axis=1)
+    src = srt[np.arange(R), pick]
+    offs = np.floor(rng.random(R) * (hap_len[src] - read_len + 1)).astype(np.int64)
+    read_off = np.concatenate([[0], np.cumsum(read_len)]).astype(np.int64)
+    tot = int(read_off[-1])
+    within = np.arange(tot) - np.repeat(read_off[:-1], read_len)
+    gidx = np.repeat(hap_off[src] + offs, read_len) + within
+    read_bases = hap_bases[gidx].copy()
+    # indel events (rare): redraw those reads with the per-read sampler
+    n_events = rng.binomial(read_len, 0.001)
+    for r in np.nonzero(n_events)[0]:
+        h = src[r]
+        seg = _sample_reads(rng, [hap_bases[hap_off[h]:hap_off[h + 1]]],
+                            np.array([read_len[r]]), np.array([0]))[0]
+        read_bases[read_off[r]:read_off[r + 1]] = seg
+    # substitutions on the reads without indel events (the redrawn ones carry their own)
+    sub = (rng.random(tot) < 0.01) & ~np.repeat(n_events > 0, read_len)
+    if sub.any():
+        cur = np.searchsorted(ACGT, read_bases[sub])
+        read_bases[sub] = ACGT[(cur + rng.integers(1, 4, size=int(sub.sum()))) % 4]
+    # all-vs-all pairs within each region
+    r_order = np.argsort(read_region, kind="stable")
+    pr, ph = [], []
+    for k in range(maxh):
+        sel = k < reg_count[read_region[r_order]]
+        rr = r_order[sel]
+        pr.append(rr)
+        ph.append(order[reg_first[read_region[rr]] + k])
+    pr = np.concatenate(pr)
+    ph = np.concatenate(ph)
+    o = np.lexsort((ph, pr))  # read-major, then haplotype
+    return {
+        "name": name,
+        "read_bases": read_bases.astype(np.uint8),
+        "base_q": bq(tot).astype(qual_dtype),
+        "ins_q": iq(tot).astype(qual_dtype),
+        "del_q": dq(tot).astype(qual_dtype),
+        "read_off": read_off,
+        "hap_bases": hap_bases.astype(np.uint8),
+        "hap_off": hap_off,
+        "pair_read": pr[o].astype(np.int32),
+        "pair_hap": ph[o].astype(np.int32),
+        "gcp": float(gcp),
+    }
+
+
 def c4_persistent(seed=4, regions=65536, n_haps=4, n_reads=16):
     """Persistent-kernel batch: 65,536 regions x 4 haplotypes x 16 reads = 2^22 pairs; read
     length log-uniform 36..300, haplotype length log-uniform 64..2048; quals as C0."""
     rng = np.random.default_rng(seed)
-    regs = []
-    for _ in range(regions):
-        hl = np.minimum(_log_uniform_int(rng, 64, 2048, n_haps), 2048)
-        rl = np.minimum(_log_uniform_int(rng, 36, 300, n_reads), 300)
-        rl = np.minimum(rl, hl.max())  # every read needs a source haplotype at least as long
-        regs.append(_region(rng, hl, rl, _bq_uniform(10, 40), _const(45)))
-    return _assemble(regs, 10.0, "c4_persistent")
+    hl = np.minimum(_log_uniform_int(rng, 64, 2048, regions * n_haps), 2048)
+    rl = np.minimum(_log_uniform_int(rng, 36, 300, regions * n_reads), 300)
+    hap_region = np.repeat(np.arange(regions), n_haps)
+    read_region = np.repeat(np.arange(regions), n_reads)
+    rl = np.minimum(rl, hl.reshape(regions, n_haps).max(axis=1)[read_region])
+    return _bulk(rng, hl, hap_region, rl, read_region, regions,
+                 lambda k: rng.integers(10, 41, size=k), lambda k: np.full(k, 45),
+                 lambda k: np.full(k, 45), 10.0, "c4_persistent")
 
 
 def make(name: str, **kw):

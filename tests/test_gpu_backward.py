@@ -117,3 +117,17 @@ def test_backward_deterministic(phmm):
     r2 = run_grad(phmm, b, dy)
     for x, y in zip(r1[1:5], r2[1:5]):
         assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+def test_reads_much_longer_than_haplotypes(phmm):
+    # m >> n forces long insertion runs: forward and adjoint mass sit in disjoint cells of a
+    # lane, beyond what one FP32 exponent per lane spans; such pairs are finished in FP64
+    rng = np.random.default_rng(9)
+    regs = []
+    for m, n in [(261, 37), (300, 64), (200, 30), (120, 20), (500, 90), (64, 8)]:
+        hap = synth.ACGT[rng.integers(0, 4, n)]
+        read = synth.ACGT[rng.integers(0, 4, m)]
+        regs.append(([hap], [read], [rng.integers(10, 41, m)], [rng.integers(30, 46, m)],
+                     [rng.integers(30, 46, m)]))
+    b = synth._assemble(regs, 10.0, "long_reads", qual_dtype=np.float32)
+    check_against_oracle(phmm, b, np.ones(len(b["pair_read"])))
