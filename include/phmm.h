@@ -96,8 +96,9 @@ typedef struct phmm_options {
   int32_t persistent;  /* 1: persistent work-queue kernels; 0: one warp group per item */
   int32_t use_graph;   /* 1: replay the launch sequence from a captured CUDA graph */
   int32_t warps_per_block; /* 0 = automatic */
-  int32_t bin_rows[PHMM_MAX_READ_LEN / 4 + 1]; /* optional tuned table (see phmm_tune) */
-  int32_t bin_table_valid; /* 1 if bin_rows holds a tuned table */
+  int32_t bin_rows[PHMM_MAX_READ_LEN / 4 + 1]; /* optional read-length -> group table */
+  int32_t bin_table_valid; /* 1 if bin_rows holds a table */
+  int32_t adjoint_rescue;  /* 1: adjoints out of the FP32 range are redone in FP64; 0: NaN */
 } phmm_options;
 
 void phmm_options_default(phmm_options *opt);

@@ -126,15 +126,14 @@ __device__ __forceinline__ void rec_load(const T *base, int lane, T (&v)[W]) {
   }
 }
 
+// Small integers (exponents, base codes) ride in the records as exact floating values.
 template <typename T>
 __device__ __forceinline__ T int_bits(int e) {
-  if constexpr (sizeof(T) == 4) return __int_as_float(e);
-  else return __longlong_as_double((long long)e);
+  return (T)e;
 }
 template <typename T>
 __device__ __forceinline__ int bits_int(T x) {
-  if constexpr (sizeof(T) == 4) return __float_as_int(x);
-  else return (int)__double_as_longlong(x);
+  return (int)x;
 }
 
 __device__ __forceinline__ int hap_code_at(const uint8_t *hcode, int64_t hs, int64_t n,
@@ -194,7 +193,7 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
   constexpr int G = 32 / L, VW = G_::VW, LS = G_::LS, CS = G_::CS;
   constexpr int kBias = 2;
   constexpr int CKW = ck_width<T>(K), CBW = cb_width<T>(K);
-  constexpr int kHmax = sizeof(T) == 4 ? 200 : 1900;  // E_fwd + E_adj the split covers
+  constexpr int kHmax = sizeof(T) == 4 ? 190 : 1900;  // E_fwd + E_adj the split covers
   constexpr unsigned FULL = 0xffffffffu;
   const FwdArgs &fa = a.f;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -434,16 +433,6 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
         rec_load<T, CBW>(cbb + (size_t)u2 * 32 * CBW, lane, rec);
         const int64_t j = (int64_t)b + u2 + 1 - t;  // this lane's column at this step
         const int c = bits_int<T>(rec[3 * K + 5]);
-        // posterior scale 2^(EF + EB), split between the adjoint and the forward factors
-        // h < -kHmax: every product is below 2^-150 of a posterior and flushes to 0, which
-        // is harmless; h > kHmax: forward and adjoint mass sit in disjoint cells of the lane
-        // and the split factors may overflow, so the pair is finished in FP64.
-        const int h = EF + as.EB;
-        if (h > kHmax && nzF && as.nz) hard = true;
-        // a lane-segment whose forward values are all zero (the wavefront has not reached it)
-        // contributes nothing; zero scales keep its adjoint tail from producing inf * 0
-        const T g1 = nzF ? Num<T>::exp2i(h >> 1) : (T)0;
-        const T g2 = nzF ? Num<T>::exp2i(h - (h >> 1)) : (T)0;
         T e[K], w[K];
         load_rows<T, K>(tblE + c * CS, e);
         load_rows<T, K>(tblW + c * CS, w);
@@ -459,6 +448,18 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
         const T ubK = as.diagU;
         as.diagU = rU;
         const T sd = (t == L - 1 && j >= 1 && j <= n) ? as.seed : (T)0;
+        // Posterior scale 2^(EF + EB), split between the adjoint and the forward factors,
+        // each at most 2^(kHmax/2) so neither factor overflows.  Where the lane's forward or
+        // adjoint values are all zero the products are zero (zero scales: no inf * 0);
+        // h < -kHmax leaves every product below 2^-150 of a posterior (flushes to 0,
+        // harmless); h > kHmax with both nonzero means forward and adjoint mass sit in
+        // disjoint cells of the lane, beyond what the split covers: the pair goes to FP64.
+        const int h = EF + as.EB;
+        const bool nzB = as.nz || rU != (T)0 || rI != (T)0 || sd != (T)0;
+        if (h > kHmax && nzF && nzB) hard = true;
+        const bool use = nzF && nzB && h <= kHmax;
+        const T g1 = use ? Num<T>::exp2i(h >> 1) : (T)0;
+        const T g2 = use ? Num<T>::exp2i(h - (h >> 1)) : (T)0;
         T ub = ubK, Ibl = rI;
         const T Mds = rec[3 * K] * g2, Sds = rec[3 * K + 1] * g2, inM = rec[3 * K + 2] * g2,
                 inI = rec[3 * K + 3] * g2;
@@ -762,7 +763,7 @@ int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, floa
       c.f.counter = (int32_t *)(ws + plan_layout_bin(pl, 7)) + cfg;
       c.nchk = (int32_t)bwd_nchk(L, nmax);
       c.slot_elems = slot_elems(L, K, 4, nmax);
-      c.rescue = 0;
+      c.rescue = o.adjoint_rescue ? 0 : 1;  // without the FP64 pass, failures write NaN
       BwdKernel k = bwd_kernel32(L, K);
       if (!k) return (int)cudaErrorInvalidValue;
       const size_t sm = bwd_smem(K, 4, block);

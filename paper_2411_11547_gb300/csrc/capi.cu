@@ -208,6 +208,7 @@ void phmm_options_default(phmm_options *opt) {
   opt->use_graph = 1;
   opt->warps_per_block = 4;
   opt->bin_table_valid = 0;
+  opt->adjoint_rescue = 1;
 }
 
 const char *phmm_status_str(int s) {

@@ -52,7 +52,7 @@ class Options(ctypes.Structure):
         ("persistent", ctypes.c_int32), ("use_graph", ctypes.c_int32),
         ("warps_per_block", ctypes.c_int32),
         ("bin_rows", ctypes.c_int32 * (PHMM_MAX_READ_LEN // 4 + 1)),
-        ("bin_table_valid", ctypes.c_int32),
+        ("bin_table_valid", ctypes.c_int32), ("adjoint_rescue", ctypes.c_int32),
     ]
 
 
