@@ -179,6 +179,40 @@ int phmm_plan_backward_ms(phmm_plan *plan, float *ms_adjoint, float *ms_reduce);
 int phmm_plan_rescue_counts(phmm_plan *plan, const void *ws, void *stream, int64_t *counts);
 
 /*
+ * Forward scoring for callers that cannot allocate device memory.
+ *
+ * Some callers may not call cudaMalloc at all: code running inside a framework that owns
+ * every device allocation through its own pool, request paths of a server where an
+ * allocation (and the device-wide synchronisation cudaMalloc/cudaFree can imply) is not
+ * allowed, or a plug-in that is only handed its input and output buffers.  This entry
+ * point needs no plan and no workspace: its scratch (per-position parameters, base codes,
+ * padded haplotype codes) lives in one static device array of PHMM_NOALLOC_SCRATCH_BYTES
+ * that every GPU loading the library holds until the process exits.  It allocates nothing
+ * (no cudaMalloc, cudaFree or allocating library call).
+ *
+ * Arguments are those of phmm_batch (device memory, caller-owned) plus out_log10[P] and
+ * out_flags[P] (device).  It scores every pair with the extended-range FP32 wavefront in one
+ * lanes x rows group sized by the longest read (no length binning, no FP64 rescue: flags
+ * are PHMM_FLAG_FP32 | PHMM_FLAG_EXTENDED, or PHMM_FLAG_INVALID for out-of-range pair ids).
+ * Bases and qualities are not validated (use phmm_plan_create for that where allocation
+ * is allowed).  It waits once on `stream` to read the batch sizes.
+ *
+ * Returns PHMM_ENOMEM if the batch's scratch (16 B per read base + 1 B per read base + the
+ * padded haplotype codes, about 1 B per haplotype base + 32 B per haplotype) exceeds
+ * PHMM_NOALLOC_SCRATCH_BYTES, PHMM_ETOOLONG for a read longer than PHMM_MAX_READ_LEN,
+ * PHMM_EINVAL for bad arguments, PHMM_ECUDA on a CUDA error.
+ *
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  Every call
+ * shares the one array, which keeps the previous call's contents: calls that overlap on
+ * the GPU (other streams or threads) race and must be serialised by the caller.  The paper
+ * has no counterpart to this entry point.
+ */
+#define PHMM_NOALLOC_SCRATCH_BYTES (64 << 20)
+int phmm_forward_noalloc(const phmm_batch *batch, double *out_log10, uint8_t *out_flags,
+                         void *stream);
+
+/*
  * Arithmetic-pipe probe (roofline denominators): lane multiply-adds per second sustained
  * by one kernel on the current device.  kind 0 = FP32 FFMA, 1 = packed fma.rn.f32x2
  * (counted as two lane operations), 2 = FP64 DFMA.  Allocates and frees a small buffer.
