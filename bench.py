@@ -30,13 +30,14 @@ sys.path.insert(0, ROOT)
 METRIC = "Pair-HMM GCUPS fwd and fwd+bwd vs plain FP32 kernel; % of FP32-pipe peak"
 UNIT = "GCUPS"
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-# FP32 pipe operations per cell, algorithmic: Eq. 1 with beta folded into the emission
-# table (FADD, FFMA, FMUL), Eq. 2 (FMUL, FFMA), Eq. 3 (FMUL, FFMA).
-FWD_OPS_PER_CELL = 7
-# Adjoint, algorithmic: the forward values of the cell (7, above) plus the reverse
+# FP32 pipe operations per cell, algorithmic.  With beta folded into the emission table and
+# the deletion state carried as D' = D/zeta: M = E (a' M_diag + S_diag) with S = I + D (2),
+# I = delta M_up + eps I_up (2), D' = M_left + eps D'_left (1), S = I + zeta D' (1): 6.
+FWD_OPS_PER_CELL = 6
+# Adjoint, algorithmic: the forward values of the cell (6, above) plus the reverse
 # recurrences (u = beta lambda M^: 1; M^: 3; I^: 1; D^: 1) plus the partials (alpha, beta:
-# 2; Q: I+D, alpha' M + S, w M^ G: 3; delta, zeta: 2; eps: 2): 7 + 6 + 9 + 1 = 23.
-BWD_OPS_PER_CELL = 23
+# 2; Q: I+D, alpha' M + S, w M^ G: 3; delta, zeta: 2; eps: 2): 6 + 6 + 9 + 1 = 22.
+BWD_OPS_PER_CELL = 22
 
 WORKLOAD_DESC = {
     "c4_persistent": "65,536 regions x 4 haplotypes x 16 reads = 2^22 pairs; read length "

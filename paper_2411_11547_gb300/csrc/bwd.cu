@@ -77,6 +77,10 @@ struct BwdArgs {
   int32_t *why;                   // [2]: hand-offs for the scale range / non-finite partials
 };
 
+// Steps per recomputed segment (after the ramp): the per-warp record buffer holds kSeg steps,
+// small enough that the records of all resident warps stay in L2.
+constexpr int kSeg = 8;
+
 // Record widths (elements, multiples of the 16-byte vector) of a checkpoint and of a
 // recorded step: K rows of M, I, D plus the boundary values.
 template <typename T>
@@ -91,26 +95,33 @@ __host__ __device__ constexpr int cb_width(int K) {
 }
 
 // Records are stored as [record][16-byte group][lane], so one warp-wide 128-bit access
-// covers 512 contiguous bytes.
-template <typename T, int W>
+// covers 512 contiguous bytes.  STREAM: checkpoints, written once and read once much later,
+// bypass the caches' keep-alive (evict-first) so the short-lived step records stay in L2.
+template <typename T, int W, bool STREAM = false>
 __device__ __forceinline__ void rec_store(T *base, int lane, const T (&v)[W]) {
   if constexpr (sizeof(T) == 4) {
 #pragma unroll
-    for (int g = 0; g < W / 4; ++g)
-      reinterpret_cast<float4 *>(base)[g * 32 + lane] =
-          make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+    for (int g = 0; g < W / 4; ++g) {
+      const float4 x = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+      if constexpr (STREAM) __stcs(reinterpret_cast<float4 *>(base) + g * 32 + lane, x);
+      else reinterpret_cast<float4 *>(base)[g * 32 + lane] = x;
+    }
   } else {
 #pragma unroll
-    for (int g = 0; g < W / 2; ++g)
-      reinterpret_cast<double2 *>(base)[g * 32 + lane] = make_double2(v[2 * g], v[2 * g + 1]);
+    for (int g = 0; g < W / 2; ++g) {
+      const double2 x = make_double2(v[2 * g], v[2 * g + 1]);
+      if constexpr (STREAM) __stcs(reinterpret_cast<double2 *>(base) + g * 32 + lane, x);
+      else reinterpret_cast<double2 *>(base)[g * 32 + lane] = x;
+    }
   }
 }
-template <typename T, int W>
+template <typename T, int W, bool STREAM = false>
 __device__ __forceinline__ void rec_load(const T *base, int lane, T (&v)[W]) {
   if constexpr (sizeof(T) == 4) {
 #pragma unroll
     for (int g = 0; g < W / 4; ++g) {
-      const float4 x = reinterpret_cast<const float4 *>(base)[g * 32 + lane];
+      const float4 x = STREAM ? __ldcs(reinterpret_cast<const float4 *>(base) + g * 32 + lane)
+                              : reinterpret_cast<const float4 *>(base)[g * 32 + lane];
       v[4 * g] = x.x;
       v[4 * g + 1] = x.y;
       v[4 * g + 2] = x.z;
@@ -119,7 +130,8 @@ __device__ __forceinline__ void rec_load(const T *base, int lane, T (&v)[W]) {
   } else {
 #pragma unroll
     for (int g = 0; g < W / 2; ++g) {
-      const double2 x = reinterpret_cast<const double2 *>(base)[g * 32 + lane];
+      const double2 x = STREAM ? __ldcs(reinterpret_cast<const double2 *>(base) + g * 32 + lane)
+                               : reinterpret_cast<const double2 *>(base)[g * 32 + lane];
       v[2 * g] = x.x;
       v[2 * g + 1] = x.y;
     }
@@ -144,10 +156,11 @@ __device__ __forceinline__ int hap_code_at(const uint8_t *hcode, int64_t hs, int
 // Adjoint state of one lane.
 template <typename T, int K>
 struct AdjState {
-  T u[K];      // u(i, j+1) = beta lambda M^ of the lane's rows at the column to the right
+  T u[K];      // u(i, j+1) = beta lambda M^ of the lane's rows at the column to the right,
+               // with the sign of the signed emission (+ match, - mismatch)
   T Db[K];     // D^(i, j+1)
   T Itop;      // I^ of the lane's top row at its current column (read by the lane above)
-  T diagU;     // u of the lower lane's top row one column to the right (own scale)
+  T diagU;     // u of the lower lane's top row one column to the right (own scale, signed)
   T fB;        // 2^(E_low - E_own) and the row bias, for values from the lane below
   T seed;      // 1/L in the stored scale of the last row (last lane only)
   int EB;      // per-lane exponent of the adjoints
@@ -161,9 +174,9 @@ template <typename T, int L, int K, int kBias>
 __device__ __forceinline__ void adj_rescale(AdjState<T, K> &as, int t, T S, int ES,
                                             bool apply = true) {
   constexpr unsigned FULL = 0xffffffffu;
-  T mx = fmax(as.Itop, as.diagU);
+  T mx = fmax(as.Itop, fabs(as.diagU));
 #pragma unroll
-  for (int r = 0; r < K; ++r) mx = fmax(mx, fmax(as.u[r], as.Db[r]));
+  for (int r = 0; r < K; ++r) mx = fmax(mx, fmax(fabs(as.u[r]), as.Db[r]));
   const bool zero = !(mx > (T)0);
   if (apply) as.nz = !zero;
   if (apply && !zero) {
@@ -178,7 +191,7 @@ __device__ __forceinline__ void adj_rescale(AdjState<T, K> &as, int t, T S, int 
     as.diagU *= sc;
     as.EB = En;
   }
-  const T xb = fmax(as.u[0], as.Itop);
+  const T xb = fmax(fabs(as.u[0]), as.Itop);
   const int Elow = __shfl_down_sync(FULL, as.EB, 1, L);
   const T xbl = __shfl_down_sync(FULL, xb, 1, L);
   if (apply && zero && t < L - 1)
@@ -199,8 +212,8 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int t = lane % L, sub = lane / L;
-  T *tblE = reinterpret_cast<T *>(smem_raw) + (size_t)warp * 2 * kCodes * CS + lane * LS;
-  T *tblW = tblE + kCodes * CS;
+  // one table per warp: signed emissions beta * lambda (+ for a match, - for a mismatch)
+  T *tblE = reinterpret_cast<T *>(smem_raw) + (size_t)warp * kCodes * CS + lane * LS;
   const int wpb = blockDim.x >> 5;
   T *slot = reinterpret_cast<T *>(a.scratch) + (size_t)(blockIdx.x * wpb + warp) * a.slot_elems;
   T *ckb = slot;
@@ -248,7 +261,7 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
     WfState<T, K> st;
 #pragma unroll
     for (int rv = 0; rv < K; rv += VW) {
-      T ev[kCodes][VW], wv[kCodes][VW];
+      T ev[kCodes][VW];
 #pragma unroll
       for (int u = 0; u < VW; ++u) {
         const int rr = rv + u;
@@ -265,15 +278,12 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
           dl[rr] *= bias;
           st.I[rr] = 0;
           const T em = bias * (beta * ((T)1 - Q)), ex = bias * (beta * (Q / (T)3));
-          const T wm = -bias * beta, wx = bias * (beta / (T)3);
 #pragma unroll
           for (int c = 0; c < kNull; ++c) {
             const bool mt = c == code || c == kN || code == kN;
-            ev[c][u] = mt ? em : ex;
-            wv[c][u] = mt ? wm : wx;
+            ev[c][u] = mt ? em : -ex;
           }
           ev[kNull][u] = 0;
-          wv[kNull][u] = 0;
         } else {
           ap[rr] = 0;
           dl[rr] = 0;
@@ -282,14 +292,11 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
           cE[rr] = 0;
           st.I[rr] = bnd * (T)(1ll << (kBias * rr));
 #pragma unroll
-          for (int c = 0; c < kCodes; ++c) ev[c][u] = wv[c][u] = 0;
+          for (int c = 0; c < kCodes; ++c) ev[c][u] = 0;
         }
       }
 #pragma unroll
-      for (int c = 0; c < kCodes; ++c) {
-        store_vec<T, VW>(tblE + c * CS + rv, ev[c]);
-        store_vec<T, VW>(tblW + c * CS + rv, wv[c]);
-      }
+      for (int c = 0; c < kCodes; ++c) store_vec<T, VW>(tblE + c * CS + rv, ev[c]);
     }
     // cE: the I -> I coefficient for the adjoint, equal to the forward's on real rows and 0
     // on pad rows (whose adjoints are never needed; the forward's pass-through coefficient
@@ -303,7 +310,7 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
     int steps = n > 0 ? (int)n + L - 1 : 0;
     steps = __reduce_max_sync(FULL, steps);
     const int ramp = steps < ((L + 15) & ~15) ? steps : ((L + 15) & ~15);
-    const int nq = ramp + (steps - ramp + 15) / 16;
+    const int nq = ramp + (steps - ramp + kSeg - 1) / kSeg;
     st.c = kNull;
     st.Md = 0;
     st.Sd = t == 0 ? bnd : (T)0;
@@ -315,8 +322,8 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
     int Efin = 0;
     bool done = false;
     for (int q = 0; q < nq; ++q) {
-      const int b = q < ramp ? q : ramp + 16 * (q - ramp);
-      const int len = q < ramp ? 1 : 16;
+      const int b = q < ramp ? q : ramp + kSeg * (q - ramp);
+      const int len = q < ramp ? 1 : kSeg;
       {
         T ck[CKW];
 #pragma unroll
@@ -331,13 +338,13 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
         ck[3 * K + 3] = int_bits<T>(st.E);
 #pragma unroll
         for (int k = 3 * K + 4; k < CKW; ++k) ck[k] = 0;
-        rec_store<T, CKW>(ckb + (size_t)q * 32 * CKW, lane, ck);
+        rec_store<T, CKW, true>(ckb + (size_t)q * 32 * CKW, lane, ck);
       }
       for (int u = 0; u < len; ++u) {
         const int s = b + u;  // 0-based step index
         const int cu = (t == 0 && s < n) ? (int)fa.hcode[hs + s] : kNull;
         T in3[3];
-        wf_step<T, L, K, true>(st, cu, t, bnd, eps, tblE, ap, dl, zt, ei, in3);
+        wf_step<T, L, K, true, false, true>(st, cu, t, bnd, eps, tblE, ap, dl, zt, ei, in3);
       }
       if (!done && b + len >= fin) {
         Sfin = st.acc;
@@ -366,9 +373,11 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
     as.seed = 0;
     as.nz = false;
     adj_rescale<T, L, K, kBias>(as, t, okS ? S : (T)0, ES);
-    T gA[K], gQ[K], gD[K], gZ[K];
+    // per-row partial sums: gA (alpha), gX / gY (emission: signed / all columns, see phase C),
+    // gD (delta), gZ (zeta)
+    T gA[K], gX[K], gY[K], gD[K], gZ[K];
 #pragma unroll
-    for (int r = 0; r < K; ++r) gA[r] = gQ[r] = gD[r] = gZ[r] = 0;
+    for (int r = 0; r < K; ++r) gA[r] = gX[r] = gY[r] = gD[r] = gZ[r] = 0;
     T gS = 0, gE = 0, gEI = 0;
     // the adjoint enters the pair's lanes one per step from its last column on: renormalise
     // after every one of the first ramp_b such steps (a window set by the pair alone, so the
@@ -376,11 +385,11 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
     const int ramp_b = 16 + ((L + 15) & ~15);
 
     for (int q = nq - 1; q >= 0; --q) {
-      const int b = q < ramp ? q : ramp + 16 * (q - ramp);
-      const int len = q < ramp ? 1 : 16;
+      const int b = q < ramp ? q : ramp + kSeg * (q - ramp);
+      const int len = q < ramp ? 1 : kSeg;
       {
         T ck[CKW];
-        rec_load<T, CKW>(ckb + (size_t)q * 32 * CKW, lane, ck);
+        rec_load<T, CKW, true>(ckb + (size_t)q * 32 * CKW, lane, ck);
 #pragma unroll
         for (int r = 0; r < K; ++r) {
           st.M[r] = ck[r];
@@ -407,7 +416,7 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
         rec[3 * K] = st.Md;
         rec[3 * K + 1] = st.Sd;
         T in3[3];
-        wf_step<T, L, K, true>(st, cu, t, bnd, eps, tblE, ap, dl, zt, ei, in3);
+        wf_step<T, L, K, true, false, true>(st, cu, t, bnd, eps, tblE, ap, dl, zt, ei, in3);
         rec[3 * K + 2] = in3[0];
         rec[3 * K + 3] = in3[1];
         rec[3 * K + 4] = in3[2];
@@ -433,9 +442,8 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
         rec_load<T, CBW>(cbb + (size_t)u2 * 32 * CBW, lane, rec);
         const int64_t j = (int64_t)b + u2 + 1 - t;  // this lane's column at this step
         const int c = bits_int<T>(rec[3 * K + 5]);
-        T e[K], w[K];
+        T e[K];
         load_rows<T, K>(tblE + c * CS, e);
-        load_rows<T, K>(tblW + c * CS, w);
         T rU = __shfl_down_sync(FULL, as.u[0], 1, L);
         T rI = __shfl_down_sync(FULL, as.Itop, 1, L);
         if (t == L - 1) {
@@ -460,6 +468,8 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
         const bool use = nzF && nzB && h <= kHmax;
         const T g1 = use ? Num<T>::exp2i(h >> 1) : (T)0;
         const T g2 = use ? Num<T>::exp2i(h - (h >> 1)) : (T)0;
+        // columns outside 1..n (code "no column") have no emission and no emission partial
+        const T g1y = c == kNull ? (T)0 : g1;
         T ub = ubK, Ibl = rI;
         const T Mds = rec[3 * K] * g2, Sds = rec[3 * K + 1] * g2, inM = rec[3 * K + 2] * g2,
                 inI = rec[3 * K + 3] * g2;
@@ -469,19 +479,23 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
           const T dlB = r == K - 1 ? dlb : dl[r + 1];
           const T eiB = r == K - 1 ? eib : cE[r + 1];
           const T add = r == K - 1 ? sd : (T)0;
-          const T Mb = apB * ub + dlB * Ibl + zt[r] * as.Db[r] + add;
-          const T Ib = ub + eiB * Ibl + add;
-          const T Dn = ub + eps * as.Db[r];
+          // u is stored with the emission's sign (the match flag); the recurrences use |u|
+          const T uba = fabs(ub);
+          const T Mb = apB * uba + dlB * Ibl + zt[r] * as.Db[r] + add;
+          const T Ib = uba + eiB * Ibl + add;
+          const T Dn = uba + eps * as.Db[r];
           const T un = e[r] * Mb;
           // partials: adjoint x 2^(h/2) times forward x 2^(h - h/2)
-          const T Mg = Mb * g1, Ig = Ib * g1, Dg = Dn * g1, ag = un * g1;
+          const T Mg = Mb * g1y, Ig = Ib * g1, Dg = Dn * g1, ag = un * g1;
           const T Mup = r ? rec[r - 1] * g2 : Mds;
           const T Sup = r ? (rec[K + r - 1] + rec[2 * K + r - 1]) * g2 : Sds;
           const T Mu = r ? cM[r - 1] * g2 : inM;
           const T Iu = r ? cI[r - 1] * g2 : inI;
-          gA[r] += ag * Mup;
-          gS += ag * Sup;
-          gQ[r] += (Mg * w[r]) * (ap[r] * Mup + Sup);
+          const T Gp = ap[r] * Mup + Sup;  // M(i,j) / (beta lambda)
+          gA[r] += fabs(ag) * Mup;
+          gS += fabs(ag) * Sup;
+          gX[r] += ag * Gp;                // signed: match columns minus mismatch columns
+          gY[r] += Mg * Gp;                // all columns
           gD[r] += Ig * Mu;
           gEI += (Ig * cE[r]) * Iu;  // eps x the I -> I partial
           gZ[r] += Dg * (rec[r] * g2);
@@ -509,8 +523,9 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
 #pragma unroll
     for (int r = 0; r < K; ++r)
       if (t * K + r - npad >= 0)
-        finite = finite && fabs(gA[r]) < (T)1e30 && fabs(gQ[r]) < (T)1e30 &&
-                 fabs(gD[r]) < (T)1e30 && fabs(gZ[r]) < (T)1e30;  // false for NaN too
+        finite = finite && fabs(gA[r]) < (T)1e30 && fabs(gX[r]) < (T)1e30 &&
+                 fabs(gY[r]) < (T)1e30 && fabs(gD[r]) < (T)1e30 &&
+                 fabs(gZ[r]) < (T)1e30;  // false for NaN too
     int hs_any = (hard || !finite) ? 1 : 0;
     int why_h = hard ? 1 : 0, why_f = finite ? 0 : 1;
 #pragma unroll
@@ -560,7 +575,15 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
             di = -(gDl - gAl) * del * (T)0.1;
             dd = -(gZ[r] - gAl) * zet * (T)0.1;
           }
-          db = -gQ[r] * Q * (T)0.1;
+          // emission partial: with em, ex the magnitudes of the (biased) match / mismatch
+          // emissions, gX = em U - ex (gY - U) where U is the match-column part of gY, so
+          // U = (gX + ex gY) / (em + ex); dE/dQ is -bias beta on matches, +bias beta / 3 on
+          // mismatches.
+          const T bias = r ? (T)(1 << kBias) : (T)1;
+          const T em = bias * (beta * ((T)1 - Q)), ex = bias * (beta * (Q / (T)3));
+          const T U = (gX[r] + ex * gY[r]) / (em + ex);
+          const T gQ = bias * beta * (gY[r] / (T)3 - U * ((T)4 / (T)3));
+          db = -gQ * Q * (T)0.1;
           a.part_bq[po + pos] = ok ? (float)(dy * (double)db) : nanv;
           a.part_iq[po + pos] = ok ? (float)(dy * (double)di) : nanv;
           a.part_dq[po + pos] = ok ? (float)(dy * (double)dd) : nanv;
@@ -597,8 +620,9 @@ static BwdKernel bwd_kernel64(int K) {
 }
 
 static size_t bwd_smem(int K, int elem, int block) {
-  const int vw = 16 / elem, units = K * elem / 16, LS = (units % 2 == 1) ? K : K + vw;
-  return (size_t)(block / 32) * 2 * kCodes * 32 * LS * elem;
+  const int vw = 16 / elem, KV = (K + vw - 1) / vw * vw, units = KV / vw;
+  const int LS = (units % 2 == 1) ? KV : KV + vw;
+  return (size_t)(block / 32) * kCodes * 32 * LS * elem;
 }
 
 // Read length -> FP32 backward group (rows per lane <= 12 keeps the adjoint in registers).
@@ -608,11 +632,8 @@ int bwd_default_cfg(int m) {
                              {96, 8, 12},  {128, 16, 8},  {192, 16, 12}, {256, 32, 8},
                              {384, 32, 12}, {512, 32, 16}};
   for (const Gp &g : order)
-    if (m <= g.cap) {
-      const int li = g.L == 4 ? 0 : g.L == 8 ? 1 : g.L == 16 ? 2 : 3;
-      return li * 5 + (g.K / 4 - 1);
-    }
-  return 3 * 5 + 3;
+    if (m <= g.cap) return cfg_index(g.L, g.K);
+  return cfg_index(32, 16);
 }
 
 static int blocks_per_sm(BwdKernel k, size_t smem, int block) {
@@ -624,15 +645,15 @@ static int blocks_per_sm(BwdKernel k, size_t smem, int block) {
 }
 
 static int64_t bwd_nchk(int L, int64_t n_max) {
-  const int64_t steps = n_max + L - 1 + 16;
+  const int64_t steps = n_max + L - 1 + kSeg;
   const int64_t ramp = (L + 15) & ~15;
-  return ramp + (steps + 15) / 16 + 2;
+  return ramp + (steps + kSeg - 1) / kSeg + 2;
 }
 
 static int64_t slot_elems(int L, int K, int elem, int64_t n_max) {
   const int vw = 16 / elem;
   const int ckw = (3 * K + 4 + vw - 1) / vw * vw, cbw = (3 * K + 6 + vw - 1) / vw * vw;
-  return bwd_nchk(L, n_max) * 32 * ckw + 16 * 32 * cbw;
+  return bwd_nchk(L, n_max) * 32 * ckw + kSeg * 32 * cbw;
 }
 
 struct BwdLayout {

@@ -38,8 +38,8 @@ static int cuda_fail(cudaError_t e) {
   } while (0)
 
 static size_t table_warp_bytes(int K, int elem) {
-  const int vw = 16 / elem, units = K * elem / 16;
-  const int LS = (units % 2 == 1) ? K : K + vw;
+  const int vw = 16 / elem, KV = (K + vw - 1) / vw * vw, units = KV / vw;
+  const int LS = (units % 2 == 1) ? KV : KV + vw;
   return (size_t)kCodes * 32 * LS * elem;
 }
 
@@ -100,21 +100,20 @@ int launch_fwd64(int cfg64, bool ext, int grid, int block, cudaStream_t s, const
   return (int)cudaGetLastError();
 }
 
-// Default read-length -> group table: the smallest lanes x rows group holding m, preferring
-// few lanes (short wavefront ramp) and many rows per lane (per-step overhead amortised).
+// Default read-length -> group table: the lanes x rows group with the fewest pad rows,
+// fewer lanes on a tie (shorter wavefront ramp, more rows to amortise each step's exchange).
 static int default_cfg_of_m(int m) {
-  struct G { int cap, L, K; };
-  static const G order[] = {{16, 4, 4},   {32, 4, 8},   {48, 4, 12},  {64, 4, 16},
-                            {80, 4, 20},  {96, 8, 12},  {128, 8, 16}, {160, 8, 20},
-                            {192, 16, 12}, {256, 16, 16}, {320, 16, 20}, {384, 32, 12},
-                            {512, 32, 16}};
-  for (const G &g : order)
-    if (m <= g.cap) {
-      int li = g.L == 4 ? 0 : g.L == 8 ? 1 : g.L == 16 ? 2 : 3;
-      int ki = g.K / 4 - 1;
-      return li * 5 + ki;
+  int best = -1, best_cap = 1 << 30;
+  for (int L = 4; L <= 32; L *= 2) {
+    int K = (m + L - 1) / L;
+    K = K < 4 ? 4 : (K + 1) / 2 * 2;
+    if (K > 20) continue;
+    if (L * K < best_cap) {
+      best_cap = L * K;
+      best = cfg_index(L, K);
     }
-  return kNumCfg32 - 1;
+  }
+  return best < 0 ? cfg_index(32, 16) : best;
 }
 
 }  // namespace phmm
@@ -226,7 +225,7 @@ const char *phmm_status_str(int s) {
 int phmm_last_cuda_error(void) { return g_last_cuda; }
 
 static bool valid_group(int L, int K) {
-  return (L == 4 || L == 8 || L == 16 || L == 32) && K >= 4 && K <= 20 && K % 4 == 0;
+  return (L == 4 || L == 8 || L == 16 || L == 32) && K >= 4 && K <= 20 && K % 2 == 0;
 }
 
 int phmm_plan_create(const phmm_batch *batch, const phmm_options *opt, void *stream,
@@ -429,8 +428,7 @@ static int enqueue_forward(phmm_plan *pl, char *ws, double *out, uint8_t *flags,
         ++launches;
       }
     } else {
-      const int li = o.lanes == 4 ? 0 : o.lanes == 8 ? 1 : o.lanes == 16 ? 2 : 3;
-      const int cfg = li * 5 + (o.rows / 4 - 1);
+      const int cfg = cfg_index(o.lanes, o.rows);
       FwdArgs c = a;
       c.count = b.n_pairs;
       const int G = 32 / o.lanes;

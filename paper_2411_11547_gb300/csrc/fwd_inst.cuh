@@ -11,9 +11,13 @@ using FwdKernel = void (*)(const FwdArgs);
 #define PHMM_FWD_ROWS_SWITCH(T, L, EXT)          \
   switch (K) {                                   \
     case 4: return wf_forward<T, L, 4, EXT>;     \
+    case 6: return wf_forward<T, L, 6, EXT>;     \
     case 8: return wf_forward<T, L, 8, EXT>;     \
+    case 10: return wf_forward<T, L, 10, EXT>;   \
     case 12: return wf_forward<T, L, 12, EXT>;   \
+    case 14: return wf_forward<T, L, 14, EXT>;   \
     case 16: return wf_forward<T, L, 16, EXT>;   \
+    case 18: return wf_forward<T, L, 18, EXT>;   \
     case 20: return wf_forward<T, L, 20, EXT>;   \
     default: return nullptr;                     \
   }

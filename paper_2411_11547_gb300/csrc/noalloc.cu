@@ -123,8 +123,8 @@ extern "C" int phmm_forward_noalloc(const phmm_batch *batch, double *out_log10,
   while ((4 << li) * 20 < max_m) ++li;
   const int L = 4 << li;
   int K = (max_m + L - 1) / L;
-  K = K < 4 ? 4 : (K + 3) / 4 * 4;
-  const int cfg = li * 5 + (K / 4 - 1);
+  K = K < 4 ? 4 : (K + 1) / 2 * 2;
+  const int cfg = cfg_index(L, K);
 
   FwdArgs a;
   std::memset(&a, 0, sizeof(a));

@@ -73,10 +73,11 @@ __host__ __device__ __forceinline__ int64_t hap_start(int64_t hap_off_h, int64_t
 // is odd.
 template <typename T, int K>
 struct TableGeom {
-  static constexpr int VW = 16 / sizeof(T);                 // elements per 128-bit load
-  static constexpr int units = K * (int)sizeof(T) / 16;
-  static constexpr int LS = (units % 2 == 1) ? K : K + VW;  // lane stride
-  static constexpr int CS = 32 * LS;                        // code-plane stride
+  static constexpr int VW = 16 / sizeof(T);                  // elements per 128-bit load
+  static constexpr int KV = (K + VW - 1) / VW * VW;          // rows rounded to whole vectors
+  static constexpr int units = KV / VW;
+  static constexpr int LS = (units % 2 == 1) ? KV : KV + VW;  // lane stride
+  static constexpr int CS = 32 * LS;                         // code-plane stride
   static constexpr size_t warp_bytes = (size_t)kCodes * CS * sizeof(T);
 };
 
@@ -91,11 +92,12 @@ __device__ __forceinline__ void store_vec<double, 2>(double *dst, const double *
   *reinterpret_cast<double2 *>(dst) = make_double2(v[0], v[1]);
 }
 
+// K rows of a lane's emission row: 128-bit loads, and a 64-bit load for two leftover floats.
 template <typename T, int K>
 __device__ __forceinline__ void load_rows(const T *src, T (&e)[K]) {
   constexpr int VW = 16 / sizeof(T);
 #pragma unroll
-  for (int r = 0; r < K; r += VW) {
+  for (int r = 0; r + VW <= K; r += VW) {
     if constexpr (sizeof(T) == 4) {
       float4 v = *reinterpret_cast<const float4 *>(src + r);
       e[r] = v.x;
@@ -108,6 +110,12 @@ __device__ __forceinline__ void load_rows(const T *src, T (&e)[K]) {
       e[r + 1] = v.y;
     }
   }
+  if constexpr (K % VW == 2 && sizeof(T) == 4) {
+    float2 v = *reinterpret_cast<const float2 *>(src + K - 2);
+    e[K - 2] = v.x;
+    e[K - 1] = v.y;
+  }
+  static_assert(K % VW == 0 || (K % VW == 2 && sizeof(T) == 4), "rows per lane");
 }
 
 __device__ __forceinline__ double qual_at(const void *q, int f32, int64_t g) {
@@ -150,7 +158,15 @@ struct WfState {
 // One wavefront step: lane t advances its K rows by one column (Eq. 1-3).
 // `in3` receives the boundary values (M, I, D of the row above at this column, in the
 // lane's own scale) for callers that record the step (the adjoint's recompute).
-template <typename T, int L, int K, bool EXT>
+//
+// PRIMED: the state holds D' = D / zeta instead of D (per row).  Eq. 3 becomes
+// D'(i,j) = M(i,j-1) + eps D'(i,j-1), one FMA instead of a multiply and an FMA, and the
+// I + D the next row needs is formed as I + zeta D' (an FMA instead of an add): 6 FP32
+// operations per cell instead of 7.  The lane below receives I + D of the last row directly
+// (in3[2] then holds I + D, not D).
+// ABS_E: the table holds signed emissions (the sign marks a match, for the adjoint); the
+// recurrence uses their magnitudes (a free operand modifier).
+template <typename T, int L, int K, bool EXT, bool PRIMED = false, bool ABS_E = false>
 __device__ __forceinline__ void wf_step(WfState<T, K> &st, int cu, int t, T bnd, T eps,
                                         const T *tbl, const T (&ap)[K], const T (&dl)[K],
                                         const T (&zt)[K], const T (&ei)[K], T (&in3)[3]) {
@@ -158,13 +174,14 @@ __device__ __forceinline__ void wf_step(WfState<T, K> &st, int cu, int t, T bnd,
   constexpr int CS = TableGeom<T, K>::CS;
   const int cin = __shfl_up_sync(FULL, st.c, 1, L);
   st.c = (t == 0) ? cu : cin;
+  const T third = PRIMED ? st.I[K - 1] + zt[K - 1] * st.D[K - 1] : st.D[K - 1];
   T inM = __shfl_up_sync(FULL, st.M[K - 1], 1, L);
   T inI = __shfl_up_sync(FULL, st.I[K - 1], 1, L);
-  T inD = __shfl_up_sync(FULL, st.D[K - 1], 1, L);
+  T inD = __shfl_up_sync(FULL, third, 1, L);
   if (t == 0) {  // row 0 (or the last pad row): M = 0, I + D = K0 * D(0, j) carried in I
     inM = 0;
     inI = bnd;
-    inD = 0;
+    inD = PRIMED ? bnd : (T)0;
   }
   if constexpr (EXT) {
     inM *= st.f;
@@ -179,15 +196,22 @@ __device__ __forceinline__ void wf_step(WfState<T, K> &st, int cu, int t, T bnd,
 #pragma unroll
   for (int r = K - 1; r >= 0; --r) {
     const T md = r ? st.M[r - 1] : st.Md;
-    const T sd = r ? st.I[r - 1] + st.D[r - 1] : st.Sd;
-    st.D[r] = zt[r] * st.M[r] + eps * st.D[r];  // Eq. 3 (same row, previous column)
-    st.M[r] = e[r] * (ap[r] * md + sd);         // Eq. 1 (previous row, previous column)
+    T sd;
+    if constexpr (PRIMED) {
+      sd = r ? st.I[r - 1] + zt[r - 1] * st.D[r - 1] : st.Sd;
+      st.D[r] = st.M[r] + eps * st.D[r];            // Eq. 3 over zeta
+    } else {
+      sd = r ? st.I[r - 1] + st.D[r - 1] : st.Sd;
+      st.D[r] = zt[r] * st.M[r] + eps * st.D[r];    // Eq. 3 (same row, previous column)
+    }
+    const T er = ABS_E ? fabs(e[r]) : e[r];
+    st.M[r] = er * (ap[r] * md + sd);               // Eq. 1 (previous row, previous column)
   }
   st.I[0] = dl[0] * inM + ei[0] * inI;  // Eq. 2 (previous row, same column)
 #pragma unroll
   for (int r = 1; r < K; ++r) st.I[r] = dl[r] * st.M[r - 1] + ei[r] * st.I[r - 1];
   st.Md = inM;
-  st.Sd = inI + inD;
+  st.Sd = PRIMED ? inD : inI + inD;
   st.acc += st.M[K - 1] + st.I[K - 1];
 }
 
@@ -224,8 +248,15 @@ __device__ __forceinline__ void wf_rescale(WfState<T, K> &st, int t) {
   st.f = Num<T>::exp2i(t == 0 ? -st.E : Eup - st.E - kBias * (K - 1));
 }
 
+// Minimum resident blocks per SM the compiler must allow (register budget): rows per lane set
+// how many per-row registers a lane holds.
+template <typename T, int K>
+constexpr int wf_min_blocks() {
+  return sizeof(T) == 8 ? 1 : (K <= 8 ? 4 : (K <= 16 ? 3 : 2));
+}
+
 template <typename T, int L, int K, bool EXT>
-__global__ void __launch_bounds__(128) wf_forward(const FwdArgs a) {
+__global__ void __launch_bounds__(128, wf_min_blocks<T, K>()) wf_forward(const FwdArgs a) {
   using G_ = TableGeom<T, K>;
   constexpr int G = 32 / L;
   constexpr int VW = G_::VW, LS = G_::LS, CS = G_::CS;
@@ -295,6 +326,11 @@ __global__ void __launch_bounds__(128) wf_forward(const FwdArgs a) {
 #pragma unroll
       for (int u = 0; u < VW; ++u) {
         const int rr = r0v + u;
+        if (rr >= K) {  // table padding past the lane's rows
+#pragma unroll
+          for (int c = 0; c < kCodes; ++c) ev[c][u] = 0;
+          continue;
+        }
         const int pos = t * K + rr - npad;  // 0-based read position; < 0: pad row
         const T bias = rr ? (T)(1 << kBias) : (T)1;
         M[rr] = 0;
@@ -360,8 +396,8 @@ __global__ void __launch_bounds__(128) wf_forward(const FwdArgs a) {
       const int q = (s >> 2) & 3;
       const uint32_t w = q == 0 ? hv.x : (q == 1 ? hv.y : (q == 2 ? hv.z : hv.w));
       T in3[3];
-      wf_step<T, L, K, EXT>(st, (w >> (8 * (s & 3))) & 0xff, t, bnd, eps, tbl, ap, dl, zt, ei,
-                            in3);
+      wf_step<T, L, K, EXT, EXT>(st, (w >> (8 * (s & 3))) & 0xff, t, bnd, eps, tbl, ap, dl, zt,
+                                 ei, in3);
       if (!done && s + 1 >= fin) {
         Sfin = st.acc;
         Efin = st.E;
@@ -375,8 +411,8 @@ __global__ void __launch_bounds__(128) wf_forward(const FwdArgs a) {
       for (int u = 0; u < 16; ++u) {
         const uint32_t w = u < 4 ? hv.x : (u < 8 ? hv.y : (u < 12 ? hv.z : hv.w));
         T in3[3];
-        wf_step<T, L, K, EXT>(st, (w >> (8 * (u & 3))) & 0xff, t, bnd, eps, tbl, ap, dl, zt, ei,
-                              in3);
+        wf_step<T, L, K, EXT, EXT>(st, (w >> (8 * (u & 3))) & 0xff, t, bnd, eps, tbl, ap, dl,
+                                   zt, ei, in3);
       }
       if (!done && s0 + 16 >= fin) {
         Sfin = st.acc;

@@ -65,7 +65,7 @@ def test_random_pairs_binned(phmm, first_line):
 
 
 @pytest.mark.parametrize("lanes", [4, 8, 16, 32])
-@pytest.mark.parametrize("rows", [4, 8, 12, 16, 20])
+@pytest.mark.parametrize("rows", [4, 6, 8, 10, 12, 14, 16, 18, 20])
 @pytest.mark.parametrize("ext", [0, 1])
 def test_every_fixed_group(phmm, lanes, rows, ext):
     cap = min(lanes * rows, 512)
