@@ -29,6 +29,7 @@
 #include <cstdint>
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 #include "phmm_internal.cuh"
 #include "wavefront.cuh"
@@ -81,8 +82,9 @@ struct BwdArgs {
 // small enough that the records of all resident warps stay in L2.
 constexpr int kSeg = 8;
 
-// Record widths (elements, multiples of the 16-byte vector) of a checkpoint and of a
-// recorded step: K rows of M, I, D plus the boundary values.
+// Record widths (elements, multiples of the 16-byte vector) of a checkpoint (K rows of M, I,
+// D plus the boundary values, the conversion factor and the exponent) and of a recorded step
+// (K rows of M, I, D).
 template <typename T>
 __host__ __device__ constexpr int vec_w() { return 16 / (int)sizeof(T); }
 template <typename T>
@@ -90,8 +92,8 @@ __host__ __device__ constexpr int ck_width(int K) {
   return (3 * K + 4 + vec_w<T>() - 1) / vec_w<T>() * vec_w<T>();
 }
 template <typename T>
-__host__ __device__ constexpr int cb_width(int K) {
-  return (3 * K + 6 + vec_w<T>() - 1) / vec_w<T>() * vec_w<T>();
+__host__ __device__ constexpr int rec_width(int K) {
+  return (3 * K + vec_w<T>() - 1) / vec_w<T>() * vec_w<T>();
 }
 
 // Records are stored as [record][16-byte group][lane], so one warp-wide 128-bit access
@@ -200,13 +202,26 @@ __device__ __forceinline__ void adj_rescale(AdjState<T, K> &as, int t, T S, int 
   as.seed = (t == L - 1 && S > (T)0) ? Num<T>::exp2i(-ES - as.EB) / S : (T)0;
 }
 
+// Minimum resident blocks per SM the compiler must allow: the per-row registers (forward
+// state, adjoints, coefficients, five partial sums) grow with the rows per lane.
+template <typename T, int K>
+constexpr int bwd_min_blocks() {
+  return sizeof(T) == 8 ? 1 : (K <= 6 ? 4 : (K <= 8 ? 3 : 2));
+}
+
 template <typename T, int L, int K>
-__global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
+__global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const BwdArgs a) {
   using G_ = TableGeom<T, K>;
   constexpr int G = 32 / L, VW = G_::VW, LS = G_::LS, CS = G_::CS;
   constexpr int kBias = 2;
-  constexpr int CKW = ck_width<T>(K), CBW = cb_width<T>(K);
-  constexpr int kHmax = sizeof(T) == 4 ? 190 : 1900;  // E_fwd + E_adj the split covers
+  constexpr int CKW = ck_width<T>(K), RW = rec_width<T>(K);
+  // Range of the posterior scale exponent h = E_fwd + E_adj over which the raw products of
+  // stored forward and adjoint values are accumulated: below kHmin a product is at most
+  // 2^(16 + kHmin) of a posterior (dropped); above kHmax the products a lane needs can fall
+  // under the type's range, and the pair is finished in FP64.
+  constexpr int kHmax = sizeof(T) == 4 ? 100 : 900;
+  constexpr int kHmin = sizeof(T) == 4 ? -100 : -900;
+  constexpr int kNoScale = -(1 << 30);
   constexpr unsigned FULL = 0xffffffffu;
   const FwdArgs &fa = a.f;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -256,8 +271,13 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
       }
     }
     const int npad = L * K - m;
+    // pad rows: the rows above row 1 (their partials are never used)
+    const int first = npad - t * K;          // local index of the lane's first real row
+    // lanes whose products can matter: those holding a real row, and the pad lane just above
+    // a first real row that starts a lane (its last row's S feeds that row's beta partial)
+    const bool real_lane = first <= K;
     const T bnd = n > 0 ? (T)1 / (T)n : (T)0;
-    T ap[K], dl[K], zt[K], ei[K], cE[K];
+    T ap[K], dl[K], zt[K], ei[K];
     WfState<T, K> st;
 #pragma unroll
     for (int rv = 0; rv < K; rv += VW) {
@@ -274,7 +294,6 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
           row_params<T>(fa, r0 + pos, ap[rr], dl[rr], zt[rr], Q);
           const int code = fa.rcode[r0 + pos];
           ei[rr] = pos == 0 ? (T)0 : eps * bias;
-          cE[rr] = ei[rr];
           dl[rr] *= bias;
           st.I[rr] = 0;
           const T em = bias * (beta * ((T)1 - Q)), ex = bias * (beta * (Q / (T)3));
@@ -289,7 +308,6 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
           dl[rr] = 0;
           zt[rr] = 0;
           ei[rr] = bias;
-          cE[rr] = 0;
           st.I[rr] = bnd * (T)(1ll << (kBias * rr));
 #pragma unroll
           for (int c = 0; c < kCodes; ++c) ev[c][u] = 0;
@@ -298,13 +316,10 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
 #pragma unroll
       for (int c = 0; c < kCodes; ++c) store_vec<T, VW>(tblE + c * CS + rv, ev[c]);
     }
-    // cE: the I -> I coefficient for the adjoint, equal to the forward's on real rows and 0
-    // on pad rows (whose adjoints are never needed; the forward's pass-through coefficient
-    // there would carry them up with growing stored magnitude).
-    // Coefficients of the row just below the strip (the lower lane's row 0, unbiased):
+    // Coefficients of the row just below the strip (the lower lane's row 0, unbiased)
     const T apb = __shfl_down_sync(FULL, ap[0], 1, L);
     const T dlb = __shfl_down_sync(FULL, dl[0], 1, L);
-    const T eib = __shfl_down_sync(FULL, cE[0], 1, L);
+    const T eib = __shfl_down_sync(FULL, ei[0], 1, L);
 
     // ---- phase A: forward with checkpoints -------------------------------------------------
     int steps = n > 0 ? (int)n + L - 1 : 0;
@@ -344,7 +359,7 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
         const int s = b + u;  // 0-based step index
         const int cu = (t == 0 && s < n) ? (int)fa.hcode[hs + s] : kNull;
         T in3[3];
-        wf_step<T, L, K, true, false, true>(st, cu, t, bnd, eps, tblE, ap, dl, zt, ei, in3);
+        wf_step<T, L, K, true, true, true>(st, cu, t, bnd, eps, tblE, ap, dl, zt, ei, in3);
       }
       if (!done && b + len >= fin) {
         Sfin = st.acc;
@@ -373,16 +388,22 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
     as.seed = 0;
     as.nz = false;
     adj_rescale<T, L, K, kBias>(as, t, okS ? S : (T)0, ES);
-    // per-row partial sums: gA (alpha), gX / gY (emission: signed / all columns, see phase C),
-    // gD (delta), gZ (zeta)
-    T gA[K], gX[K], gY[K], gD[K], gZ[K];
+    // Partial sums, each held as (true value) x 2^-H, the lane's accumulator scale.
+    // Per row r: gA (alpha_r: u(r,j+1) M(r-1,j)), gD (delta_r: I^(r,j) M(r-1,j)),
+    // gZ (zeta_r: D^(r,j+1) M(r,j)), gY (M^(r,j) M(r,j)), gX (its mismatch-column part
+    // times -e_mismatch).  gAl / gDl: the products for the lower lane's row 0.
+    // Lane scalars: gS (beta: u S of the row above), gEI (eps via I), gED (eps via D).
+    T gA[K], gD[K], gZ[K], gY[K], gX[K];
 #pragma unroll
-    for (int r = 0; r < K; ++r) gA[r] = gX[r] = gY[r] = gD[r] = gZ[r] = 0;
-    T gS = 0, gE = 0, gEI = 0;
+    for (int r = 0; r < K; ++r) gA[r] = gD[r] = gZ[r] = gY[r] = gX[r] = 0;
+    T gAl = 0, gDl = 0, gS = 0, gEI = 0, gED = 0;
+    int H = kNoScale;
     // the adjoint enters the pair's lanes one per step from its last column on: renormalise
     // after every one of the first ramp_b such steps (a window set by the pair alone, so the
     // result does not depend on which pairs share the warp), then at segment boundaries
     const int ramp_b = 16 + ((L + 15) & ~15);
+    // lane 0's row above its strip (row 0 of the DP, or a pad row): S = K0 D(0, j)
+    const T bndS = t == 0 ? bnd : (T)0;
 
     for (int q = nq - 1; q >= 0; --q) {
       const int b = q < ramp ? q : ramp + kSeg * (q - ramp);
@@ -402,46 +423,41 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
         st.E = bits_int<T>(ck[3 * K + 3]);
       }
       st.c = hap_code_at(fa.hcode, hs, n, (int64_t)b - t);
-      // recompute the segment, recording each step's inputs
+      T mxF = fmax(st.Md, st.Sd);
+#pragma unroll
+      for (int r = 0; r < K; ++r) mxF = fmax(mxF, fmax(st.M[r], fmax(st.I[r], st.D[r])));
+      // recompute the segment, recording the lane's rows after each step (column b+u2+1-t)
+      // and the step's haplotype code (3 bits per step)
+      static_assert(3 * kSeg <= 31, "codes of a segment must fit one register");
+      int codes = 0;
       for (int u2 = 0; u2 < len; ++u2) {
         const int s = b + u2;
         const int cu = (t == 0 && s < n) ? (int)fa.hcode[hs + s] : kNull;
-        T rec[CBW];
+        T in3[3];
+        wf_step<T, L, K, true, true, true>(st, cu, t, bnd, eps, tblE, ap, dl, zt, ei, in3);
+        codes |= st.c << (3 * u2);
+        T rec[RW];
 #pragma unroll
         for (int r = 0; r < K; ++r) {
           rec[r] = st.M[r];
           rec[K + r] = st.I[r];
           rec[2 * K + r] = st.D[r];
         }
-        rec[3 * K] = st.Md;
-        rec[3 * K + 1] = st.Sd;
-        T in3[3];
-        wf_step<T, L, K, true, false, true>(st, cu, t, bnd, eps, tblE, ap, dl, zt, ei, in3);
-        rec[3 * K + 2] = in3[0];
-        rec[3 * K + 3] = in3[1];
-        rec[3 * K + 4] = in3[2];
-        rec[3 * K + 5] = int_bits<T>(st.c);
 #pragma unroll
-        for (int k = 3 * K + 6; k < CBW; ++k) rec[k] = 0;
-        rec_store<T, CBW>(cbb + (size_t)u2 * 32 * CBW, lane, rec);
+        for (int k = 3 * K; k < RW; ++k) rec[k] = 0;
+        rec_store<T, RW>(cbb + (size_t)u2 * 32 * RW, lane, rec);
       }
       const int EF = st.E;
-      T mxF = fmax(st.Md, st.Sd);
+      const T fS = bndS * Num<T>::exp2i(-EF);  // lane 0's boundary row in its own scale
 #pragma unroll
       for (int r = 0; r < K; ++r) mxF = fmax(mxF, fmax(st.M[r], fmax(st.I[r], st.D[r])));
       const bool nzF = mxF > (T)0;
-      T cM[K], cI[K];
-#pragma unroll
-      for (int r = 0; r < K; ++r) {
-        cM[r] = st.M[r];
-        cI[r] = st.I[r];
-      }
       // reverse over the segment
       for (int u2 = len - 1; u2 >= 0; --u2) {
-        T rec[CBW];
-        rec_load<T, CBW>(cbb + (size_t)u2 * 32 * CBW, lane, rec);
         const int64_t j = (int64_t)b + u2 + 1 - t;  // this lane's column at this step
-        const int c = bits_int<T>(rec[3 * K + 5]);
+        const int c = (codes >> (3 * u2)) & 7;
+        T rec[RW];
+        rec_load<T, RW>(cbb + (size_t)u2 * 32 * RW, lane, rec);
         T e[K];
         load_rows<T, K>(tblE + c * CS, e);
         T rU = __shfl_down_sync(FULL, as.u[0], 1, L);
@@ -456,76 +472,131 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
         const T ubK = as.diagU;
         as.diagU = rU;
         const T sd = (t == L - 1 && j >= 1 && j <= n) ? as.seed : (T)0;
-        // Posterior scale 2^(EF + EB), split between the adjoint and the forward factors,
-        // each at most 2^(kHmax/2) so neither factor overflows.  Where the lane's forward or
-        // adjoint values are all zero the products are zero (zero scales: no inf * 0);
-        // h < -kHmax leaves every product below 2^-150 of a posterior (flushes to 0,
-        // harmless); h > kHmax with both nonzero means forward and adjoint mass sit in
-        // disjoint cells of the lane, beyond what the split covers: the pair goes to FP64.
+        // Posterior scale 2^(EF + EB): products of stored forward and adjoint values are
+        // accumulated raw, the accumulators re-based when the scale changes.  Lanes whose
+        // forward or adjoint values are all zero contribute nothing; h > kHmax with both
+        // nonzero means forward and adjoint mass sit in disjoint cells of the lane, beyond
+        // the type's range: the pair goes to FP64.
         const int h = EF + as.EB;
         const bool nzB = as.nz || rU != (T)0 || rI != (T)0 || sd != (T)0;
-        if (h > kHmax && nzF && nzB) hard = true;
-        const bool use = nzF && nzB && h <= kHmax;
-        const T g1 = use ? Num<T>::exp2i(h >> 1) : (T)0;
-        const T g2 = use ? Num<T>::exp2i(h - (h >> 1)) : (T)0;
-        // columns outside 1..n (code "no column") have no emission and no emission partial
-        const T g1y = c == kNull ? (T)0 : g1;
+        const bool live = real_lane && nzF && nzB;
+        if (live && h > kHmax) hard = true;
+        if (live && h >= kHmin && h <= kHmax && h != H) {
+          // re-base the sums from 2^-H to 2^-h (all zero while H is unset); a shift beyond
+          // the type's exponent range is applied in two exact halves
+          auto rebase = [&](T sc) {
+#pragma unroll
+            for (int r = 0; r < K; ++r) {
+              gA[r] *= sc;
+              gD[r] *= sc;
+              gZ[r] *= sc;
+              gY[r] *= sc;
+              gX[r] *= sc;
+            }
+            gAl *= sc;
+            gDl *= sc;
+            gS *= sc;
+            gEI *= sc;
+            gED *= sc;
+          };
+          if (H != kNoScale) {
+            int d = H - h;
+            if (d > kHmax + 20 || d < -(kHmax + 20)) {
+              rebase(Num<T>::exp2i(d / 2));
+              d -= d / 2;
+            }
+            rebase(Num<T>::exp2i(d));
+          }
+          H = h;
+        }
+        // Products are added unless the step's posterior scale is negligible (h < kHmin on a
+        // live lane).  Lanes that are not live add zeros (all forward or all adjoint values
+        // zero), garbage that is discarded (pad lanes) or garbage of a pair that goes to FP64
+        // (h > kHmax): no per-row branch.
+        const bool quiet = live && h < kHmin;
         T ub = ubK, Ibl = rI;
-        const T Mds = rec[3 * K] * g2, Sds = rec[3 * K + 1] * g2, inM = rec[3 * K + 2] * g2,
-                inI = rec[3 * K + 3] * g2;
+        auto rows = [&](auto prod_tag) {
+          constexpr bool PROD = decltype(prod_tag)::value;
 #pragma unroll
-        for (int r = K - 1; r >= 0; --r) {
-          const T apB = r == K - 1 ? apb : ap[r + 1];
-          const T dlB = r == K - 1 ? dlb : dl[r + 1];
-          const T eiB = r == K - 1 ? eib : cE[r + 1];
-          const T add = r == K - 1 ? sd : (T)0;
-          // u is stored with the emission's sign (the match flag); the recurrences use |u|
-          const T uba = fabs(ub);
-          const T Mb = apB * uba + dlB * Ibl + zt[r] * as.Db[r] + add;
-          const T Ib = uba + eiB * Ibl + add;
-          const T Dn = uba + eps * as.Db[r];
-          const T un = e[r] * Mb;
-          // partials: adjoint x 2^(h/2) times forward x 2^(h - h/2)
-          const T Mg = Mb * g1y, Ig = Ib * g1, Dg = Dn * g1, ag = un * g1;
-          const T Mup = r ? rec[r - 1] * g2 : Mds;
-          const T Sup = r ? (rec[K + r - 1] + rec[2 * K + r - 1]) * g2 : Sds;
-          const T Mu = r ? cM[r - 1] * g2 : inM;
-          const T Iu = r ? cI[r - 1] * g2 : inI;
-          const T Gp = ap[r] * Mup + Sup;  // M(i,j) / (beta lambda)
-          gA[r] += fabs(ag) * Mup;
-          gS += fabs(ag) * Sup;
-          gX[r] += ag * Gp;                // signed: match columns minus mismatch columns
-          gY[r] += Mg * Gp;                // all columns
-          gD[r] += Ig * Mu;
-          gEI += (Ig * cE[r]) * Iu;  // eps x the I -> I partial
-          gZ[r] += Dg * (rec[r] * g2);
-          gE += Dg * (rec[2 * K + r] * g2);
-          ub = as.u[r];
-          as.u[r] = un;
-          as.Db[r] = Dn;
-          Ibl = Ib;
-        }
+          for (int r = K - 1; r >= 0; --r) {
+            const T apB = r == K - 1 ? apb : ap[r + 1];
+            const T dlB = r == K - 1 ? dlb : dl[r + 1];
+            const T eiB = r == K - 1 ? eib : ei[r + 1];
+            const T add = r == K - 1 ? sd : (T)0;
+            const T uba = fabs(ub);       // u(r+1, j+1); u carries the emission's sign
+            const T Il = eiB * Ibl;       // eps x I^(r+1, j)
+            const T zD = zt[r] * as.Db[r];
+            const T Mv = rec[r], Iv = rec[K + r], Dv = rec[2 * K + r];  // forward, column j
+            const T Mb = apB * uba + dlB * Ibl + zD + add;               // M^(r, j)
+            const T Ib = uba + Il + add;                                 // I^(r, j)
+            const T Dn = uba + eps * as.Db[r];                           // D^(r, j)
+            const T un = e[r] * Mb;                                      // u(r, j)
+            if constexpr (PROD) {
+              if (r == K - 1) {
+                gAl += uba * Mv;
+                gDl += Ibl * Mv;
+              } else {
+                gA[r + 1] += uba * Mv;
+                gD[r + 1] += Ibl * Mv;
+              }
+              gS += uba * (Iv + zt[r] * Dv);
+              // the I -> I partial counts only where the row below is a real row (pad rows
+              // pass the boundary down with a nonzero coefficient)
+              gEI += (r + 1 > first ? Il : (T)0) * Iv;
+              gZ[r] += as.Db[r] * Mv;
+              gED += zD * Dv;
+              gY[r] += Mb * Mv;
+              gX[r] += fmin(un, (T)0) * Mv;
+            }
+            ub = as.u[r];
+            as.u[r] = un;
+            as.Db[r] = Dn;
+            Ibl = Ib;
+          }
+          // lane 0's row above: u(0, j+1) times the boundary S = K0 D(0, j)
+          if constexpr (PROD) gS += fabs(ub) * fS;
+        };
+        if (!quiet)
+          rows(std::true_type{});
+        else
+          rows(std::false_type{});
         as.Itop = Ibl;
-#pragma unroll
-        for (int r = 0; r < K; ++r) {
-          cM[r] = rec[r];
-          cI[r] = rec[K + r];
-        }
         const int sf = b + u2 + 1;  // forward step just reversed
         const bool apply = sf <= fin && (u2 == 0 || sf > fin - ramp_b);
-        adj_rescale<T, L, K, kBias>(as, t, okS ? S : (T)0, ES, apply);
+        if (__any_sync(FULL, apply)) adj_rescale<T, L, K, kBias>(as, t, okS ? S : (T)0, ES, apply);
       }
     }
 
     // ---- phase C: chain rule to the Phred inputs, per-pair partials ------------------------
-    T gSs = gS, gEs = gE + gEI / eps;
+    // accumulators to true values; the products of a row's I^ with the row above's M carry
+    // one row bias less than the others (x 2^kBias), except across the lane edge
+    const T sc = H == kNoScale ? (T)0 : Num<T>::exp2i(H);
+    gAl *= sc;
+    gDl *= sc;
+    T dAlpha[K], dDelta[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+      dAlpha[r] = gA[r] * sc;
+      dDelta[r] = gD[r] * (sc * (T)(1 << kBias));
+      gZ[r] *= sc;
+      gY[r] *= sc;
+      gX[r] *= sc;
+    }
+    {
+      const T aup = __shfl_up_sync(FULL, gAl, 1, L);
+      const T dup = __shfl_up_sync(FULL, gDl, 1, L);
+      dAlpha[0] = t == 0 ? (T)0 : aup;
+      dDelta[0] = t == 0 ? (T)0 : dup;
+    }
+    // pad lanes' scalar sums are garbage by construction
+    T gSs = real_lane ? gS * sc : (T)0, gEs = real_lane ? (gED + gEI / eps) * sc : (T)0;
     bool finite = true;  // over the real rows (pad rows' sums are never used)
 #pragma unroll
     for (int r = 0; r < K; ++r)
-      if (t * K + r - npad >= 0)
-        finite = finite && fabs(gA[r]) < (T)1e30 && fabs(gX[r]) < (T)1e30 &&
-                 fabs(gY[r]) < (T)1e30 && fabs(gD[r]) < (T)1e30 &&
-                 fabs(gZ[r]) < (T)1e30;  // false for NaN too
+      if (r >= first)
+        finite = finite && fabs(dAlpha[r]) < (T)1e30 && fabs(dDelta[r]) < (T)1e30 &&
+                 fabs(gZ[r]) < (T)1e30 && fabs(gY[r]) < (T)1e30 &&
+                 fabs(gX[r]) < (T)1e30;  // false for NaN too
     int hs_any = (hard || !finite) ? 1 : 0;
     int why_h = hard ? 1 : 0, why_f = finite ? 0 : 1;
 #pragma unroll
@@ -536,6 +607,7 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
       why_h |= __shfl_xor_sync(FULL, why_h, o, L);
       why_f |= __shfl_xor_sync(FULL, why_f, o, L);
     }
+    // d ln L / d eps = gE - gS / beta (beta = 1 - eps); d eps / d gcp = -(ln 10 / 10) eps
     const T dgcp_l = -(gEs - gSs / beta) * eps * (T)0.1;
     if (!(fabs(dgcp_l) < (T)1e30)) hs_any = 1;
     if (valid && !bad) {
@@ -561,29 +633,29 @@ __global__ void __launch_bounds__(128) wf_backward(const BwdArgs a) {
           if (pos < 0) continue;
           T dum, del, zet, Q;
           row_params<T>(fa, r0 + pos, dum, del, zet, Q);
-          const T gAl = gA[r] / beta;
-          const T gDl = gD[r] * (r ? (T)(1 << kBias) : (T)1);
-          T db, di, dd;
+          const T gAlpha = dAlpha[r] / beta;  // d ln L / d alpha_r
+          T di, dd;
           if (fa.alpha_mode) {
             const T iq = (T)qual_at(fa.iq, fa.qual_f32, r0 + pos);
             const T dq = (T)qual_at(fa.dq, fa.qual_f32, r0 + pos);
             const T pa = sizeof(T) == 4 ? (T)exp10f((float)(-(iq + dq) * (T)0.1))
                                         : (T)exp10(-(double)(iq + dq) / 10.0);
-            di = -(gDl * del - gAl * pa) * (T)0.1;
-            dd = -(gZ[r] * zet - gAl * pa) * (T)0.1;
+            di = -(dDelta[r] * del - gAlpha * pa) * (T)0.1;
+            dd = -(gZ[r] * zet - gAlpha * pa) * (T)0.1;
           } else {
-            di = -(gDl - gAl) * del * (T)0.1;
-            dd = -(gZ[r] - gAl) * zet * (T)0.1;
+            di = -(dDelta[r] - gAlpha) * del * (T)0.1;
+            dd = -(gZ[r] - gAlpha) * zet * (T)0.1;
           }
-          // emission partial: with em, ex the magnitudes of the (biased) match / mismatch
-          // emissions, gX = em U - ex (gY - U) where U is the match-column part of gY, so
-          // U = (gX + ex gY) / (em + ex); dE/dQ is -bias beta on matches, +bias beta / 3 on
-          // mismatches.
+          // emission partial: with A1, A2 the match / mismatch parts of sum_j M^ M (the
+          // posterior occupancy of M), d ln L / dQ = -A1 / (1 - Q) + A2 / Q, since
+          // lambda = 1 - Q on a match and Q / 3 on a mismatch.  gX holds -ex A2 with ex
+          // the row's stored (biased) mismatch emission.
           const T bias = r ? (T)(1 << kBias) : (T)1;
-          const T em = bias * (beta * ((T)1 - Q)), ex = bias * (beta * (Q / (T)3));
-          const T U = (gX[r] + ex * gY[r]) / (em + ex);
-          const T gQ = bias * beta * (gY[r] / (T)3 - U * ((T)4 / (T)3));
-          db = -gQ * Q * (T)0.1;
+          const T ex = bias * (beta * (Q / (T)3));
+          const T A2 = -gX[r] / ex;
+          const T A1 = gY[r] - A2;
+          // d log10 L / d bq = (d ln L / dQ) (-Q / 10)
+          const T db = (A1 * (Q / ((T)1 - Q)) - A2) * (T)0.1;
           a.part_bq[po + pos] = ok ? (float)(dy * (double)db) : nanv;
           a.part_iq[po + pos] = ok ? (float)(dy * (double)di) : nanv;
           a.part_dq[po + pos] = ok ? (float)(dy * (double)dd) : nanv;
@@ -652,7 +724,7 @@ static int64_t bwd_nchk(int L, int64_t n_max) {
 
 static int64_t slot_elems(int L, int K, int elem, int64_t n_max) {
   const int vw = 16 / elem;
-  const int ckw = (3 * K + 4 + vw - 1) / vw * vw, cbw = (3 * K + 6 + vw - 1) / vw * vw;
+  const int ckw = (3 * K + 4 + vw - 1) / vw * vw, cbw = (3 * K + vw - 1) / vw * vw;
   return bwd_nchk(L, n_max) * 32 * ckw + kSeg * 32 * cbw;
 }
 

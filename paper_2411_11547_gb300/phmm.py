@@ -152,6 +152,35 @@ class DeviceBatch:
         self.gcp = float(batch["gcp"])
         self.alpha_mode = int(batch.get("alpha_mode", 0))
 
+    @classmethod
+    def from_tensors(cls, read_bases, base_q, ins_q, del_q, read_off, hap_bases, hap_off,
+                     pair_read, pair_hap, gcp, alpha_mode=0):
+        """Wrap tensors already on the device (no copy).  The quals are uint8 or float32; the
+        offsets int64, the pair lists int32, all contiguous."""
+        import torch
+        self = cls.__new__(cls)
+        self.host = None
+        if base_q.dtype == torch.float32:
+            self.qual_dtype = QUAL_F32
+        elif base_q.dtype == torch.uint8:
+            self.qual_dtype = QUAL_U8
+        else:
+            raise TypeError(f"quals must be uint8 or float32, got {base_q.dtype}")
+        want = {"read_bases": torch.uint8, "base_q": base_q.dtype, "ins_q": base_q.dtype,
+                "del_q": base_q.dtype, "read_off": torch.int64, "hap_bases": torch.uint8,
+                "hap_off": torch.int64, "pair_read": torch.int32, "pair_hap": torch.int32}
+        loc = dict(read_bases=read_bases, base_q=base_q, ins_q=ins_q, del_q=del_q,
+                   read_off=read_off, hap_bases=hap_bases, hap_off=hap_off,
+                   pair_read=pair_read, pair_hap=pair_hap)
+        for k, dt in want.items():
+            t = loc[k]
+            if t.dtype != dt or not t.is_contiguous() or t.device != read_bases.device:
+                raise TypeError(f"{k}: need a contiguous {dt} tensor on {read_bases.device}")
+            setattr(self, k, t)
+        self.gcp = float(gcp)
+        self.alpha_mode = int(alpha_mode)
+        return self
+
     @property
     def n_pairs(self):
         return int(self.pair_read.numel())

@@ -70,3 +70,26 @@ def test_forward_rejects_null_plan(lib):
     assert lib.phmm_forward(None, None, 0, None, None, None) == phmm.PHMM_EINVAL
     assert lib.phmm_backward(None, None, 0, None, None, None, None, None, None) == phmm.PHMM_EINVAL
     assert lib.phmm_workspace_bytes(None) == 0
+
+
+def test_autograd_wrapper_checks_tensor_layout():
+    import numpy as np
+    import torch
+    from paper_2411_11547_gb300 import phmm as ph, synth
+    from paper_2411_11547_gb300.autograd import PairHMMLogLik, layout_from_host
+    assert issubclass(PairHMMLogLik, torch.autograd.Function)
+    b = synth.random_pairs(3, 4, (5, 10), (5, 10), qual_dtype=np.float32)
+    layout, (bq, iq, dq) = layout_from_host(b, device="cpu")
+    db = ph.DeviceBatch.from_tensors(layout["read_bases"], bq, iq, dq, layout["read_off"],
+                                     layout["hap_bases"], layout["hap_off"],
+                                     layout["pair_read"], layout["pair_hap"], b["gcp"])
+    assert db.n_pairs == 4 and db.qual_dtype == ph.QUAL_F32
+    with pytest.raises(TypeError):
+        ph.DeviceBatch.from_tensors(layout["read_bases"], bq.double(), iq, dq,
+                                    layout["read_off"], layout["hap_bases"], layout["hap_off"],
+                                    layout["pair_read"], layout["pair_hap"], b["gcp"])
+    with pytest.raises(TypeError):
+        ph.DeviceBatch.from_tensors(layout["read_bases"], bq, iq, dq,
+                                    layout["read_off"].int(), layout["hap_bases"],
+                                    layout["hap_off"], layout["pair_read"], layout["pair_hap"],
+                                    b["gcp"])

@@ -131,3 +131,24 @@ def test_reads_much_longer_than_haplotypes(phmm):
                      [rng.integers(30, 46, m)]))
     b = synth._assemble(regs, 10.0, "long_reads", qual_dtype=np.float32)
     check_against_oracle(phmm, b, np.ones(len(b["pair_read"])))
+
+
+def test_autograd_function(phmm):
+    import torch
+    from paper_2411_11547_gb300.autograd import PairHMMLogLik, layout_from_host
+    b = synth.random_pairs(91, 120, (1, 250), (1, 400), related=0.6, qual_dtype=np.float32)
+    w = np.random.default_rng(4).normal(size=len(b["pair_read"]))
+    layout, (bq, iq, dq) = layout_from_host(b)
+    for t in (bq, iq, dq):
+        t.requires_grad_(True)
+    gcp = torch.tensor(float(b["gcp"]), dtype=torch.float64, requires_grad=True)
+    y, flags = PairHMMLogLik.apply(bq, iq, dq, gcp, layout)
+    loss = (y * torch.as_tensor(w, device=y.device)).sum()
+    loss.backward()
+    wy, wb, wi, wd, wg = oracle.backward_batch(b, w)
+    assert np.all(np.abs(y.detach().cpu().numpy() - wy) <= 1e-3)
+    assert flags.dtype == torch.uint8 and not flags.requires_grad
+    grad_close(bq.grad.cpu().numpy(), wb, "d/dbq")
+    grad_close(iq.grad.cpu().numpy(), wi, "d/diq")
+    grad_close(dq.grad.cpu().numpy(), wd, "d/ddq")
+    assert abs(float(gcp.grad) - wg) <= RTOL * abs(wg) + 1e-9
