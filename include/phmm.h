@@ -99,6 +99,8 @@ typedef struct phmm_options {
   int32_t bin_rows[PHMM_MAX_READ_LEN / 4 + 1]; /* optional read-length -> group table */
   int32_t bin_table_valid; /* 1 if bin_rows holds a table */
   int32_t adjoint_rescue;  /* 1: adjoints out of the FP32 range are redone in FP64; 0: NaN */
+  int32_t bwd_rows[PHMM_MAX_READ_LEN / 4 + 1]; /* optional read-length -> adjoint group table */
+  int32_t bwd_table_valid; /* 1 if bwd_rows holds a table */
 } phmm_options;
 
 void phmm_options_default(phmm_options *opt);
@@ -177,6 +179,24 @@ int phmm_plan_backward_ms(phmm_plan *plan, float *ms_adjoint, float *ms_reduce);
  * finished in FP64, counts[3] reserved (0).
  */
 int phmm_plan_rescue_counts(phmm_plan *plan, const void *ws, void *stream, int64_t *counts);
+
+/*
+ * Autotune the read-length -> group tables for this batch's length mix (Sec. III-C picks
+ * rows per thread by read length; here the choice is measured).  For every 16-row
+ * read-length range that holds pairs, a strided sample of at most `sample_pairs` of its
+ * pairs is gathered into a compact device batch and each built group (lanes x rows) whose
+ * capacity covers the range, up to twice the range's longest read, is timed with CUDA
+ * events around phmm_forward (which & 1) and phmm_backward (which & 2).  The fastest group
+ * of each range is written into opt->bin_rows / opt->bwd_rows (other entries: -1, meaning
+ * the built-in default, or the caller's previous entries) and bin_table_valid /
+ * bwd_table_valid are set.  The other fields of *opt are used as given.
+ *
+ * The batch is validated as by phmm_plan_create (same errors).  Allocates temporary device
+ * memory with cudaMallocAsync on `stream`, copies the offsets and pair lists to the host
+ * and synchronises `stream` repeatedly: run it once per workload shape, before timing.
+ */
+int phmm_autotune(const phmm_batch *batch, phmm_options *opt, int which, int64_t sample_pairs,
+                  void *stream);
 
 /*
  * Forward scoring for callers that cannot allocate device memory.

@@ -6,33 +6,36 @@
 //   M^(i,j) = a'_{i+1} u(i+1,j+1) + delta_{i+1} I^(i+1,j) + zeta_i D^(i,j+1)   [+1/L, i = m]
 //   I^(i,j) = u(i+1,j+1) + eps I^(i+1,j)                                       [+1/L, i = m]
 //   D^(i,j) = u(i+1,j+1) + eps D^(i,j+1),        u(i,j) = beta lambda(i,j) M^(i,j)
-// and each parameter's partial is a sum over cells of an adjoint times a forward value:
-//   alpha_i: sum_j M^ lambda M(i-1,j-1)      beta: sum M^ lambda (I+D)(i-1,j-1)
-//   Q_i: sum_j M^ (alpha M + beta (I+D))(i-1,j-1) dlambda/dQ     delta_i: sum_j I^ M(i-1,j)
-//   zeta_i: sum_j D^ M(i,j-1)                eps: sum I^ I(i-1,j) + D^ D(i,j-1)
-// followed by the chain rule through alpha = 1-(delta+zeta) (or 1-10^(-(iq+dq)/10)),
-// beta = 1-eps and P = 10^(-q/10).
+// and each parameter's partial is a sum over cells of an adjoint times a forward value.
+// Written so that every product pairs forward values of one column j with adjoints already
+// at hand when the reverse sweep reaches column j (u and D^ of column j+1, I^ of column j):
+//   alpha_{i+1}: sum_j u(i+1,j+1) M(i,j) / beta      beta: sum u(i+1,j+1) (I+D)(i,j) / beta
+//   delta_{i+1}: sum_j I^(i+1,j) M(i,j)              zeta_i: sum_j D^(i,j+1) M(i,j)
+//   eps: sum I^(i+1,j) I(i,j) + D^(i,j+1) D(i,j)     (minus the beta term: beta = 1 - eps)
+//   Q_i: -A1/(1-Q_i) + A2/Q_i with A1, A2 = sum over match / mismatch columns of
+//        M^(i,j) M(i,j)  (lambda = 1-Q on a match, Q/3 on a mismatch),
+// followed by the chain rule through alpha = 1-(delta+zeta) (or 1-10^(-(iq+dq)/10)) and
+// P = 10^(-q/10).
 //
 // GPU design.  The same lane/row decomposition as the forward wavefront, reversed: lane t
 // owns K rows, walks the columns from right to left, and exchanges the top row's u and I^
 // with the lane above by __shfl_down_sync.  Forward values are recomputed, not stored:
 //   phase A  runs the per-lane-exponent FP32 forward and checkpoints every lane's register
-//            state at each renormalisation point (every step of the ramp, then every 16
-//            steps) into a per-warp scratch slot;
+//            state at each renormalisation point (every step of the ramp, then every kSeg
+//            steps) into a per-warp scratch slot (streaming stores);
 //   phase B  for each segment, last to first: restores the checkpoint, recomputes the
-//            segment while recording each step's inputs (a column per step, L2-resident),
-//            then runs the adjoint over the segment in reverse and accumulates the partials.
+//            segment while recording the lane's rows (M, I, D/zeta) after each step
+//            (L2-resident), then runs the adjoint over the segment in reverse.
 // Adjoints carry their own per-lane power-of-two exponent and the inverse of the forward's
-// per-row bias, so forward x adjoint products are posterior-scale numbers; each segment's
-// products are scaled by 2^(E_fwd + E_adj).  Per-pair partials are written in FP32 and
-// reduced per read in FP64 (grad_reduce.cu).
+// per-row bias, so a forward x adjoint product is a posterior-scale number times
+// 2^-(E_fwd + E_adj).  The partial sums are held at the lane's current scale and re-based
+// (by an exact power of two) when E_fwd + E_adj changes: no per-cell scaling.  Per-pair
+// partials are written in FP32 and reduced per read in FP64 (grad_reduce.cu).
 #include <cstdint>
 #include <algorithm>
 #include <cstring>
-#include <type_traits>
 #include <vector>
-#include "phmm_internal.cuh"
-#include "wavefront.cuh"
+#include "bwd_kernel.cuh"
 
 struct phmm_plan;
 
@@ -63,632 +66,22 @@ int reduce_gradients(const phmm_batch &b, char *scratch, const float *part_bq,
                      int *launches);
 size_t reduce_scratch_bytes_aligned(int64_t P, int64_t R);
 
-struct BwdArgs {
-  FwdArgs f;               // pair list, inputs and prepared parameters (as the forward)
-  const double *dL;        // d(loss)/d(log10 L_p)
-  const int64_t *poff;     // partial-gradient offsets per pair
-  float *part_bq, *part_iq, *part_dq;
-  double *pair_dgcp;
-  void *scratch;           // per-warp slots (elements of the kernel's type)
-  int64_t slot_elems;
-  int32_t nchk;            // checkpoint capacity per slot
-  int32_t rescue;          // 1: this is the FP64 pass (write NaN on failure)
-  int32_t *resc_list[kNumCfg64];  // FP32 pass: pairs handed to the FP64 pass
-  int32_t *resc_count;
-  int32_t *why;                   // [2]: hand-offs for the scale range / non-finite partials
-};
-
-// Steps per recomputed segment (after the ramp): the per-warp record buffer holds kSeg steps,
-// small enough that the records of all resident warps stay in L2.
-constexpr int kSeg = 8;
-
-// Record widths (elements, multiples of the 16-byte vector) of a checkpoint (K rows of M, I,
-// D plus the boundary values, the conversion factor and the exponent) and of a recorded step
-// (K rows of M, I, D).
-template <typename T>
-__host__ __device__ constexpr int vec_w() { return 16 / (int)sizeof(T); }
-template <typename T>
-__host__ __device__ constexpr int ck_width(int K) {
-  return (3 * K + 4 + vec_w<T>() - 1) / vec_w<T>() * vec_w<T>();
-}
-template <typename T>
-__host__ __device__ constexpr int rec_width(int K) {
-  return (3 * K + vec_w<T>() - 1) / vec_w<T>() * vec_w<T>();
-}
-
-// Records are stored as [record][16-byte group][lane], so one warp-wide 128-bit access
-// covers 512 contiguous bytes.  STREAM: checkpoints, written once and read once much later,
-// bypass the caches' keep-alive (evict-first) so the short-lived step records stay in L2.
-template <typename T, int W, bool STREAM = false>
-__device__ __forceinline__ void rec_store(T *base, int lane, const T (&v)[W]) {
-  if constexpr (sizeof(T) == 4) {
-#pragma unroll
-    for (int g = 0; g < W / 4; ++g) {
-      const float4 x = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
-      if constexpr (STREAM) __stcs(reinterpret_cast<float4 *>(base) + g * 32 + lane, x);
-      else reinterpret_cast<float4 *>(base)[g * 32 + lane] = x;
-    }
-  } else {
-#pragma unroll
-    for (int g = 0; g < W / 2; ++g) {
-      const double2 x = make_double2(v[2 * g], v[2 * g + 1]);
-      if constexpr (STREAM) __stcs(reinterpret_cast<double2 *>(base) + g * 32 + lane, x);
-      else reinterpret_cast<double2 *>(base)[g * 32 + lane] = x;
-    }
-  }
-}
-template <typename T, int W, bool STREAM = false>
-__device__ __forceinline__ void rec_load(const T *base, int lane, T (&v)[W]) {
-  if constexpr (sizeof(T) == 4) {
-#pragma unroll
-    for (int g = 0; g < W / 4; ++g) {
-      const float4 x = STREAM ? __ldcs(reinterpret_cast<const float4 *>(base) + g * 32 + lane)
-                              : reinterpret_cast<const float4 *>(base)[g * 32 + lane];
-      v[4 * g] = x.x;
-      v[4 * g + 1] = x.y;
-      v[4 * g + 2] = x.z;
-      v[4 * g + 3] = x.w;
-    }
-  } else {
-#pragma unroll
-    for (int g = 0; g < W / 2; ++g) {
-      const double2 x = STREAM ? __ldcs(reinterpret_cast<const double2 *>(base) + g * 32 + lane)
-                               : reinterpret_cast<const double2 *>(base)[g * 32 + lane];
-      v[2 * g] = x.x;
-      v[2 * g + 1] = x.y;
-    }
-  }
-}
-
-// Small integers (exponents, base codes) ride in the records as exact floating values.
-template <typename T>
-__device__ __forceinline__ T int_bits(int e) {
-  return (T)e;
-}
-template <typename T>
-__device__ __forceinline__ int bits_int(T x) {
-  return (int)x;
-}
-
-__device__ __forceinline__ int hap_code_at(const uint8_t *hcode, int64_t hs, int64_t n,
-                                           int64_t j /* 1-based column */) {
-  return (j >= 1 && j <= n) ? (int)hcode[hs + j - 1] : kNull;
-}
-
-// Adjoint state of one lane.
-template <typename T, int K>
-struct AdjState {
-  T u[K];      // u(i, j+1) = beta lambda M^ of the lane's rows at the column to the right,
-               // with the sign of the signed emission (+ match, - mismatch)
-  T Db[K];     // D^(i, j+1)
-  T Itop;      // I^ of the lane's top row at its current column (read by the lane above)
-  T diagU;     // u of the lower lane's top row one column to the right (own scale, signed)
-  T fB;        // 2^(E_low - E_own) and the row bias, for values from the lane below
-  T seed;      // 1/L in the stored scale of the last row (last lane only)
-  int EB;      // per-lane exponent of the adjoints
-  bool nz;     // the lane held a nonzero adjoint at the latest renormalisation
-};
-
-// Renormalise the adjoints of a lane by a power of two; a lane that holds only zeros takes
-// the exponent that makes the next values from the lane below arrive near 1.
-// `apply` selects the lanes that renormalise now (the exchange runs on every lane).
-template <typename T, int L, int K, int kBias>
-__device__ __forceinline__ void adj_rescale(AdjState<T, K> &as, int t, T S, int ES,
-                                            bool apply = true) {
-  constexpr unsigned FULL = 0xffffffffu;
-  T mx = fmax(as.Itop, fabs(as.diagU));
-#pragma unroll
-  for (int r = 0; r < K; ++r) mx = fmax(mx, fmax(fabs(as.u[r]), as.Db[r]));
-  const bool zero = !(mx > (T)0);
-  if (apply) as.nz = !zero;
-  if (apply && !zero) {
-    const int En = as.EB + Num<T>::ilog2(mx);
-    const T sc = Num<T>::exp2i(as.EB - En);
-#pragma unroll
-    for (int r = 0; r < K; ++r) {
-      as.u[r] *= sc;
-      as.Db[r] *= sc;
-    }
-    as.Itop *= sc;
-    as.diagU *= sc;
-    as.EB = En;
-  }
-  const T xb = fmax(fabs(as.u[0]), as.Itop);
-  const int Elow = __shfl_down_sync(FULL, as.EB, 1, L);
-  const T xbl = __shfl_down_sync(FULL, xb, 1, L);
-  if (apply && zero && t < L - 1)
-    as.EB = Elow - kBias * (K - 1) + (xbl > (T)0 ? Num<T>::ilog2(xbl) : 0);
-  as.fB = t < L - 1 ? Num<T>::exp2i(Elow - as.EB - kBias * (K - 1)) : (T)0;
-  as.seed = (t == L - 1 && S > (T)0) ? Num<T>::exp2i(-ES - as.EB) / S : (T)0;
-}
-
-// Minimum resident blocks per SM the compiler must allow: the per-row registers (forward
-// state, adjoints, coefficients, five partial sums) grow with the rows per lane.
-template <typename T, int K>
-constexpr int bwd_min_blocks() {
-  return sizeof(T) == 8 ? 1 : (K <= 6 ? 4 : (K <= 8 ? 3 : 2));
-}
-
-template <typename T, int L, int K>
-__global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const BwdArgs a) {
-  using G_ = TableGeom<T, K>;
-  constexpr int G = 32 / L, VW = G_::VW, LS = G_::LS, CS = G_::CS;
-  constexpr int kBias = 2;
-  constexpr int CKW = ck_width<T>(K), RW = rec_width<T>(K);
-  // Range of the posterior scale exponent h = E_fwd + E_adj over which the raw products of
-  // stored forward and adjoint values are accumulated: below kHmin a product is at most
-  // 2^(16 + kHmin) of a posterior (dropped); above kHmax the products a lane needs can fall
-  // under the type's range, and the pair is finished in FP64.
-  constexpr int kHmax = sizeof(T) == 4 ? 100 : 900;
-  constexpr int kHmin = sizeof(T) == 4 ? -100 : -900;
-  constexpr int kNoScale = -(1 << 30);
-  constexpr unsigned FULL = 0xffffffffu;
-  const FwdArgs &fa = a.f;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int t = lane % L, sub = lane / L;
-  // one table per warp: signed emissions beta * lambda (+ for a match, - for a mismatch)
-  T *tblE = reinterpret_cast<T *>(smem_raw) + (size_t)warp * kCodes * CS + lane * LS;
-  const int wpb = blockDim.x >> 5;
-  T *slot = reinterpret_cast<T *>(a.scratch) + (size_t)(blockIdx.x * wpb + warp) * a.slot_elems;
-  T *ckb = slot;
-  T *cbb = slot + (size_t)a.nchk * 32 * CKW;
-  const T eps = sizeof(T) == 4 ? (T)fa.eps32 : (T)fa.eps64;
-  const T beta = sizeof(T) == 4 ? (T)fa.beta32 : (T)fa.beta64;
-
-  const int64_t count = *fa.count_dev;
-  const int64_t base = fa.offset_dev ? *fa.offset_dev : 0;
-  const int64_t nitems = (count + G - 1) / G;
-
-  for (;;) {
-    int it = 0;
-    if (lane == 0) it = atomicAdd(fa.counter, 1);
-    const int64_t item = __shfl_sync(FULL, it, 0);
-    if (item >= nitems) break;
-
-    // ---- pair and per-row constants ------------------------------------------------------
-    const int64_t idx = item * G + sub;
-    const bool valid = idx < count;
-    int32_t p = -1;
-    bool bad = false;
-    int m = 0;
-    int64_t n = 0, r0 = 0, hs = 0;
-    if (valid) {
-      p = fa.list[base + idx];
-      const int32_t ri = fa.pair_read[p], hi = fa.pair_hap[p];
-      if (ri >= 0 && ri < fa.n_reads && hi >= 0 && hi < fa.n_haps) {
-        r0 = fa.read_off[ri];
-        m = (int)(fa.read_off[ri + 1] - r0);
-        hs = hap_start(fa.hap_off[hi], hi);
-        n = fa.hap_off[hi + 1] - fa.hap_off[hi];
-        if (m <= 0 || m > L * K || n <= 0) bad = true;
-      } else {
-        bad = true;
-      }
-      if (bad) {
-        m = 0;
-        n = 0;
-      }
-    }
-    const int npad = L * K - m;
-    // pad rows: the rows above row 1 (their partials are never used)
-    const int first = npad - t * K;          // local index of the lane's first real row
-    // lanes whose products can matter: those holding a real row, and the pad lane just above
-    // a first real row that starts a lane (its last row's S feeds that row's beta partial)
-    const bool real_lane = first <= K;
-    const T bnd = n > 0 ? (T)1 / (T)n : (T)0;
-    T ap[K], dl[K], zt[K], ei[K];
-    WfState<T, K> st;
-#pragma unroll
-    for (int rv = 0; rv < K; rv += VW) {
-      T ev[kCodes][VW];
-#pragma unroll
-      for (int u = 0; u < VW; ++u) {
-        const int rr = rv + u;
-        const int pos = t * K + rr - npad;
-        const T bias = rr ? (T)(1 << kBias) : (T)1;
-        st.M[rr] = 0;
-        st.D[rr] = 0;
-        if (pos >= 0) {
-          T Q;
-          row_params<T>(fa, r0 + pos, ap[rr], dl[rr], zt[rr], Q);
-          const int code = fa.rcode[r0 + pos];
-          ei[rr] = pos == 0 ? (T)0 : eps * bias;
-          dl[rr] *= bias;
-          st.I[rr] = 0;
-          const T em = bias * (beta * ((T)1 - Q)), ex = bias * (beta * (Q / (T)3));
-#pragma unroll
-          for (int c = 0; c < kNull; ++c) {
-            const bool mt = c == code || c == kN || code == kN;
-            ev[c][u] = mt ? em : -ex;
-          }
-          ev[kNull][u] = 0;
-        } else {
-          ap[rr] = 0;
-          dl[rr] = 0;
-          zt[rr] = 0;
-          ei[rr] = bias;
-          st.I[rr] = bnd * (T)(1ll << (kBias * rr));
-#pragma unroll
-          for (int c = 0; c < kCodes; ++c) ev[c][u] = 0;
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < kCodes; ++c) store_vec<T, VW>(tblE + c * CS + rv, ev[c]);
-    }
-    // Coefficients of the row just below the strip (the lower lane's row 0, unbiased)
-    const T apb = __shfl_down_sync(FULL, ap[0], 1, L);
-    const T dlb = __shfl_down_sync(FULL, dl[0], 1, L);
-    const T eib = __shfl_down_sync(FULL, ei[0], 1, L);
-
-    // ---- phase A: forward with checkpoints -------------------------------------------------
-    int steps = n > 0 ? (int)n + L - 1 : 0;
-    steps = __reduce_max_sync(FULL, steps);
-    const int ramp = steps < ((L + 15) & ~15) ? steps : ((L + 15) & ~15);
-    const int nq = ramp + (steps - ramp + kSeg - 1) / kSeg;
-    st.c = kNull;
-    st.Md = 0;
-    st.Sd = t == 0 ? bnd : (T)0;
-    st.acc = 0;
-    st.f = t == 0 ? (T)1 : Num<T>::exp2i(-kBias * (K - 1));
-    st.E = 0;
-    const int fin = n > 0 ? (int)n + L - 1 : 0;
-    T Sfin = 0;
-    int Efin = 0;
-    bool done = false;
-    for (int q = 0; q < nq; ++q) {
-      const int b = q < ramp ? q : ramp + kSeg * (q - ramp);
-      const int len = q < ramp ? 1 : kSeg;
-      {
-        T ck[CKW];
-#pragma unroll
-        for (int r = 0; r < K; ++r) {
-          ck[r] = st.M[r];
-          ck[K + r] = st.I[r];
-          ck[2 * K + r] = st.D[r];
-        }
-        ck[3 * K] = st.Md;
-        ck[3 * K + 1] = st.Sd;
-        ck[3 * K + 2] = st.f;
-        ck[3 * K + 3] = int_bits<T>(st.E);
-#pragma unroll
-        for (int k = 3 * K + 4; k < CKW; ++k) ck[k] = 0;
-        rec_store<T, CKW, true>(ckb + (size_t)q * 32 * CKW, lane, ck);
-      }
-      for (int u = 0; u < len; ++u) {
-        const int s = b + u;  // 0-based step index
-        const int cu = (t == 0 && s < n) ? (int)fa.hcode[hs + s] : kNull;
-        T in3[3];
-        wf_step<T, L, K, true, true, true>(st, cu, t, bnd, eps, tblE, ap, dl, zt, ei, in3);
-      }
-      if (!done && b + len >= fin) {
-        Sfin = st.acc;
-        Efin = st.E;
-        done = true;
-      }
-      wf_rescale<T, L, K, kBias>(st, t);
-    }
-    if (!done) {
-      Sfin = st.acc;
-      Efin = st.E;
-    }
-    // L = S * 2^(ES - kBias (K-1)), held by the last lane of the group
-    const T S = __shfl_sync(FULL, Sfin, sub * L + L - 1);
-    const int ES = __shfl_sync(FULL, Efin, sub * L + L - 1);
-    const bool okS = S > (T)0 && S < (sizeof(T) == 4 ? (T)3.0e38f : (T)1.7e308);
-    bool hard = !okS;
-
-    // ---- phase B: adjoint, segment by segment from the right ------------------------------
-    AdjState<T, K> as;
-#pragma unroll
-    for (int r = 0; r < K; ++r) as.u[r] = as.Db[r] = 0;
-    as.Itop = as.diagU = 0;
-    as.EB = t == L - 1 ? -ES : 0;
-    as.fB = 0;
-    as.seed = 0;
-    as.nz = false;
-    adj_rescale<T, L, K, kBias>(as, t, okS ? S : (T)0, ES);
-    // Partial sums, each held as (true value) x 2^-H, the lane's accumulator scale.
-    // Per row r: gA (alpha_r: u(r,j+1) M(r-1,j)), gD (delta_r: I^(r,j) M(r-1,j)),
-    // gZ (zeta_r: D^(r,j+1) M(r,j)), gY (M^(r,j) M(r,j)), gX (its mismatch-column part
-    // times -e_mismatch).  gAl / gDl: the products for the lower lane's row 0.
-    // Lane scalars: gS (beta: u S of the row above), gEI (eps via I), gED (eps via D).
-    T gA[K], gD[K], gZ[K], gY[K], gX[K];
-#pragma unroll
-    for (int r = 0; r < K; ++r) gA[r] = gD[r] = gZ[r] = gY[r] = gX[r] = 0;
-    T gAl = 0, gDl = 0, gS = 0, gEI = 0, gED = 0;
-    int H = kNoScale;
-    // the adjoint enters the pair's lanes one per step from its last column on: renormalise
-    // after every one of the first ramp_b such steps (a window set by the pair alone, so the
-    // result does not depend on which pairs share the warp), then at segment boundaries
-    const int ramp_b = 16 + ((L + 15) & ~15);
-    // lane 0's row above its strip (row 0 of the DP, or a pad row): S = K0 D(0, j)
-    const T bndS = t == 0 ? bnd : (T)0;
-
-    for (int q = nq - 1; q >= 0; --q) {
-      const int b = q < ramp ? q : ramp + kSeg * (q - ramp);
-      const int len = q < ramp ? 1 : kSeg;
-      {
-        T ck[CKW];
-        rec_load<T, CKW, true>(ckb + (size_t)q * 32 * CKW, lane, ck);
-#pragma unroll
-        for (int r = 0; r < K; ++r) {
-          st.M[r] = ck[r];
-          st.I[r] = ck[K + r];
-          st.D[r] = ck[2 * K + r];
-        }
-        st.Md = ck[3 * K];
-        st.Sd = ck[3 * K + 1];
-        st.f = ck[3 * K + 2];
-        st.E = bits_int<T>(ck[3 * K + 3]);
-      }
-      st.c = hap_code_at(fa.hcode, hs, n, (int64_t)b - t);
-      T mxF = fmax(st.Md, st.Sd);
-#pragma unroll
-      for (int r = 0; r < K; ++r) mxF = fmax(mxF, fmax(st.M[r], fmax(st.I[r], st.D[r])));
-      // recompute the segment, recording the lane's rows after each step (column b+u2+1-t)
-      // and the step's haplotype code (3 bits per step)
-      static_assert(3 * kSeg <= 31, "codes of a segment must fit one register");
-      int codes = 0;
-      for (int u2 = 0; u2 < len; ++u2) {
-        const int s = b + u2;
-        const int cu = (t == 0 && s < n) ? (int)fa.hcode[hs + s] : kNull;
-        T in3[3];
-        wf_step<T, L, K, true, true, true>(st, cu, t, bnd, eps, tblE, ap, dl, zt, ei, in3);
-        codes |= st.c << (3 * u2);
-        T rec[RW];
-#pragma unroll
-        for (int r = 0; r < K; ++r) {
-          rec[r] = st.M[r];
-          rec[K + r] = st.I[r];
-          rec[2 * K + r] = st.D[r];
-        }
-#pragma unroll
-        for (int k = 3 * K; k < RW; ++k) rec[k] = 0;
-        rec_store<T, RW>(cbb + (size_t)u2 * 32 * RW, lane, rec);
-      }
-      const int EF = st.E;
-      const T fS = bndS * Num<T>::exp2i(-EF);  // lane 0's boundary row in its own scale
-#pragma unroll
-      for (int r = 0; r < K; ++r) mxF = fmax(mxF, fmax(st.M[r], fmax(st.I[r], st.D[r])));
-      const bool nzF = mxF > (T)0;
-      // reverse over the segment
-      for (int u2 = len - 1; u2 >= 0; --u2) {
-        const int64_t j = (int64_t)b + u2 + 1 - t;  // this lane's column at this step
-        const int c = (codes >> (3 * u2)) & 7;
-        T rec[RW];
-        rec_load<T, RW>(cbb + (size_t)u2 * 32 * RW, lane, rec);
-        T e[K];
-        load_rows<T, K>(tblE + c * CS, e);
-        T rU = __shfl_down_sync(FULL, as.u[0], 1, L);
-        T rI = __shfl_down_sync(FULL, as.Itop, 1, L);
-        if (t == L - 1) {
-          rU = 0;
-          rI = 0;
-        } else {
-          rU *= as.fB;
-          rI *= as.fB;
-        }
-        const T ubK = as.diagU;
-        as.diagU = rU;
-        const T sd = (t == L - 1 && j >= 1 && j <= n) ? as.seed : (T)0;
-        // Posterior scale 2^(EF + EB): products of stored forward and adjoint values are
-        // accumulated raw, the accumulators re-based when the scale changes.  Lanes whose
-        // forward or adjoint values are all zero contribute nothing; h > kHmax with both
-        // nonzero means forward and adjoint mass sit in disjoint cells of the lane, beyond
-        // the type's range: the pair goes to FP64.
-        const int h = EF + as.EB;
-        const bool nzB = as.nz || rU != (T)0 || rI != (T)0 || sd != (T)0;
-        const bool live = real_lane && nzF && nzB;
-        if (live && h > kHmax) hard = true;
-        if (live && h >= kHmin && h <= kHmax && h != H) {
-          // re-base the sums from 2^-H to 2^-h (all zero while H is unset); a shift beyond
-          // the type's exponent range is applied in two exact halves
-          auto rebase = [&](T sc) {
-#pragma unroll
-            for (int r = 0; r < K; ++r) {
-              gA[r] *= sc;
-              gD[r] *= sc;
-              gZ[r] *= sc;
-              gY[r] *= sc;
-              gX[r] *= sc;
-            }
-            gAl *= sc;
-            gDl *= sc;
-            gS *= sc;
-            gEI *= sc;
-            gED *= sc;
-          };
-          if (H != kNoScale) {
-            int d = H - h;
-            if (d > kHmax + 20 || d < -(kHmax + 20)) {
-              rebase(Num<T>::exp2i(d / 2));
-              d -= d / 2;
-            }
-            rebase(Num<T>::exp2i(d));
-          }
-          H = h;
-        }
-        // Products are added unless the step's posterior scale is negligible (h < kHmin on a
-        // live lane).  Lanes that are not live add zeros (all forward or all adjoint values
-        // zero), garbage that is discarded (pad lanes) or garbage of a pair that goes to FP64
-        // (h > kHmax): no per-row branch.
-        const bool quiet = live && h < kHmin;
-        T ub = ubK, Ibl = rI;
-        auto rows = [&](auto prod_tag) {
-          constexpr bool PROD = decltype(prod_tag)::value;
-#pragma unroll
-          for (int r = K - 1; r >= 0; --r) {
-            const T apB = r == K - 1 ? apb : ap[r + 1];
-            const T dlB = r == K - 1 ? dlb : dl[r + 1];
-            const T eiB = r == K - 1 ? eib : ei[r + 1];
-            const T add = r == K - 1 ? sd : (T)0;
-            const T uba = fabs(ub);       // u(r+1, j+1); u carries the emission's sign
-            const T Il = eiB * Ibl;       // eps x I^(r+1, j)
-            const T zD = zt[r] * as.Db[r];
-            const T Mv = rec[r], Iv = rec[K + r], Dv = rec[2 * K + r];  // forward, column j
-            const T Mb = apB * uba + dlB * Ibl + zD + add;               // M^(r, j)
-            const T Ib = uba + Il + add;                                 // I^(r, j)
-            const T Dn = uba + eps * as.Db[r];                           // D^(r, j)
-            const T un = e[r] * Mb;                                      // u(r, j)
-            if constexpr (PROD) {
-              if (r == K - 1) {
-                gAl += uba * Mv;
-                gDl += Ibl * Mv;
-              } else {
-                gA[r + 1] += uba * Mv;
-                gD[r + 1] += Ibl * Mv;
-              }
-              gS += uba * (Iv + zt[r] * Dv);
-              // the I -> I partial counts only where the row below is a real row (pad rows
-              // pass the boundary down with a nonzero coefficient)
-              gEI += (r + 1 > first ? Il : (T)0) * Iv;
-              gZ[r] += as.Db[r] * Mv;
-              gED += zD * Dv;
-              gY[r] += Mb * Mv;
-              gX[r] += fmin(un, (T)0) * Mv;
-            }
-            ub = as.u[r];
-            as.u[r] = un;
-            as.Db[r] = Dn;
-            Ibl = Ib;
-          }
-          // lane 0's row above: u(0, j+1) times the boundary S = K0 D(0, j)
-          if constexpr (PROD) gS += fabs(ub) * fS;
-        };
-        if (!quiet)
-          rows(std::true_type{});
-        else
-          rows(std::false_type{});
-        as.Itop = Ibl;
-        const int sf = b + u2 + 1;  // forward step just reversed
-        const bool apply = sf <= fin && (u2 == 0 || sf > fin - ramp_b);
-        if (__any_sync(FULL, apply)) adj_rescale<T, L, K, kBias>(as, t, okS ? S : (T)0, ES, apply);
-      }
-    }
-
-    // ---- phase C: chain rule to the Phred inputs, per-pair partials ------------------------
-    // accumulators to true values; the products of a row's I^ with the row above's M carry
-    // one row bias less than the others (x 2^kBias), except across the lane edge
-    const T sc = H == kNoScale ? (T)0 : Num<T>::exp2i(H);
-    gAl *= sc;
-    gDl *= sc;
-    T dAlpha[K], dDelta[K];
-#pragma unroll
-    for (int r = 0; r < K; ++r) {
-      dAlpha[r] = gA[r] * sc;
-      dDelta[r] = gD[r] * (sc * (T)(1 << kBias));
-      gZ[r] *= sc;
-      gY[r] *= sc;
-      gX[r] *= sc;
-    }
-    {
-      const T aup = __shfl_up_sync(FULL, gAl, 1, L);
-      const T dup = __shfl_up_sync(FULL, gDl, 1, L);
-      dAlpha[0] = t == 0 ? (T)0 : aup;
-      dDelta[0] = t == 0 ? (T)0 : dup;
-    }
-    // pad lanes' scalar sums are garbage by construction
-    T gSs = real_lane ? gS * sc : (T)0, gEs = real_lane ? (gED + gEI / eps) * sc : (T)0;
-    bool finite = true;  // over the real rows (pad rows' sums are never used)
-#pragma unroll
-    for (int r = 0; r < K; ++r)
-      if (r >= first)
-        finite = finite && fabs(dAlpha[r]) < (T)1e30 && fabs(dDelta[r]) < (T)1e30 &&
-                 fabs(gZ[r]) < (T)1e30 && fabs(gY[r]) < (T)1e30 &&
-                 fabs(gX[r]) < (T)1e30;  // false for NaN too
-    int hs_any = (hard || !finite) ? 1 : 0;
-    int why_h = hard ? 1 : 0, why_f = finite ? 0 : 1;
-#pragma unroll
-    for (int o = 1; o < L; o <<= 1) {
-      gSs += __shfl_xor_sync(FULL, gSs, o, L);
-      gEs += __shfl_xor_sync(FULL, gEs, o, L);
-      hs_any |= __shfl_xor_sync(FULL, hs_any, o, L);
-      why_h |= __shfl_xor_sync(FULL, why_h, o, L);
-      why_f |= __shfl_xor_sync(FULL, why_f, o, L);
-    }
-    // d ln L / d eps = gE - gS / beta (beta = 1 - eps); d eps / d gcp = -(ln 10 / 10) eps
-    const T dgcp_l = -(gEs - gSs / beta) * eps * (T)0.1;
-    if (!(fabs(dgcp_l) < (T)1e30)) hs_any = 1;
-    if (valid && !bad) {
-      const bool to_rescue = hs_any && !a.rescue;
-      if (to_rescue) {
-        if (t == 0) {
-          const int bin = bin64_of_m(m);
-          const int pos = atomicAdd(&a.resc_count[bin], 1);
-          a.resc_list[bin][pos] = p;
-          if (a.why) {
-            if (why_h) atomicAdd(&a.why[0], 1);
-            if (why_f) atomicAdd(&a.why[1], 1);
-          }
-        }
-      } else {
-        const double dy = a.dL[p];
-        const int64_t po = a.poff[p];
-        const bool ok = !hs_any;
-        const float nanv = __int_as_float(0x7fc00000);
-#pragma unroll
-        for (int r = 0; r < K; ++r) {
-          const int pos = t * K + r - npad;
-          if (pos < 0) continue;
-          T dum, del, zet, Q;
-          row_params<T>(fa, r0 + pos, dum, del, zet, Q);
-          const T gAlpha = dAlpha[r] / beta;  // d ln L / d alpha_r
-          T di, dd;
-          if (fa.alpha_mode) {
-            const T iq = (T)qual_at(fa.iq, fa.qual_f32, r0 + pos);
-            const T dq = (T)qual_at(fa.dq, fa.qual_f32, r0 + pos);
-            const T pa = sizeof(T) == 4 ? (T)exp10f((float)(-(iq + dq) * (T)0.1))
-                                        : (T)exp10(-(double)(iq + dq) / 10.0);
-            di = -(dDelta[r] * del - gAlpha * pa) * (T)0.1;
-            dd = -(gZ[r] * zet - gAlpha * pa) * (T)0.1;
-          } else {
-            di = -(dDelta[r] - gAlpha) * del * (T)0.1;
-            dd = -(gZ[r] - gAlpha) * zet * (T)0.1;
-          }
-          // emission partial: with A1, A2 the match / mismatch parts of sum_j M^ M (the
-          // posterior occupancy of M), d ln L / dQ = -A1 / (1 - Q) + A2 / Q, since
-          // lambda = 1 - Q on a match and Q / 3 on a mismatch.  gX holds -ex A2 with ex
-          // the row's stored (biased) mismatch emission.
-          const T bias = r ? (T)(1 << kBias) : (T)1;
-          const T ex = bias * (beta * (Q / (T)3));
-          const T A2 = -gX[r] / ex;
-          const T A1 = gY[r] - A2;
-          // d log10 L / d bq = (d ln L / dQ) (-Q / 10)
-          const T db = (A1 * (Q / ((T)1 - Q)) - A2) * (T)0.1;
-          a.part_bq[po + pos] = ok ? (float)(dy * (double)db) : nanv;
-          a.part_iq[po + pos] = ok ? (float)(dy * (double)di) : nanv;
-          a.part_dq[po + pos] = ok ? (float)(dy * (double)dd) : nanv;
-        }
-        if (t == 0) a.pair_dgcp[p] = ok ? dy * (double)dgcp_l : (double)nanv;
-      }
-    }
-  }
-}
-
 // ------------------------------------------------------------------------ host side ------
 
-using BwdKernel = void (*)(const BwdArgs);
-
-// FP32 groups: lanes 4..32 x rows 4/8/12 (16 for the longest reads); FP64 hand-off groups:
-// 32 lanes x rows 4/8/16 (reads up to 128/256/512).
 static BwdKernel bwd_kernel32(int L, int K) {
-#define PHMM_BWD_CASE(LL, KK) \
-  if (L == LL && K == KK) return wf_backward<float, LL, KK>;
-  PHMM_BWD_CASE(4, 4) PHMM_BWD_CASE(4, 8) PHMM_BWD_CASE(4, 12)
-  PHMM_BWD_CASE(8, 4) PHMM_BWD_CASE(8, 8) PHMM_BWD_CASE(8, 12)
-  PHMM_BWD_CASE(16, 4) PHMM_BWD_CASE(16, 8) PHMM_BWD_CASE(16, 12)
-  PHMM_BWD_CASE(32, 4) PHMM_BWD_CASE(32, 8) PHMM_BWD_CASE(32, 12) PHMM_BWD_CASE(32, 16)
-#undef PHMM_BWD_CASE
-  return nullptr;
-}
-static BwdKernel bwd_kernel64(int K) {
-  switch (K) {
-    case 4: return wf_backward<double, 32, 4>;
-    case 8: return wf_backward<double, 32, 8>;
-    case 16: return wf_backward<double, 32, 16>;
+  switch (L) {
+    case 4:
+    case 8: return bwd32_lo(L, K);
+    case 16: return bwd32_mid(L, K);
+    case 32: return bwd32_hi(L, K);
     default: return nullptr;
   }
+}
+static BwdKernel bwd_kernel64(int K) { return bwd64_table(K); }
+
+// 1 if the FP32 adjoint is built for group `cfg`.
+int bwd_cfg_supported(int cfg) {
+  return cfg >= 0 && cfg < kNumCfg32 && bwd_kernel32(cfg_lanes(cfg), cfg_rows(cfg)) != nullptr;
 }
 
 static size_t bwd_smem(int K, int elem, int block) {

@@ -24,6 +24,7 @@ int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, floa
                      cudaEvent_t *ev3);
 size_t bwd_workspace_bytes(const phmm_plan *pl);
 int bwd_default_cfg(int m);
+int bwd_cfg_supported(int cfg);
 
 static thread_local int g_last_cuda = 0;
 
@@ -314,7 +315,14 @@ int phmm_plan_create(const phmm_batch *batch, const phmm_options *opt, void *str
       if (used[c]) pl->used_cfgs.push_back(c);
   }
   {
-    for (int m = 0; m <= PHMM_MAX_READ_LEN; ++m) pl->bwd_cfg_of_m[m] = bwd_default_cfg(std::max(m, 1));
+    for (int m = 0; m <= PHMM_MAX_READ_LEN; ++m) {
+      int c = bwd_default_cfg(std::max(m, 1));
+      if (o.bwd_table_valid) {
+        const int e = o.bwd_rows[(std::max(m, 1) + 3) / 4];
+        if (bwd_cfg_supported(e) && cfg_lanes(e) * cfg_rows(e) >= m) c = e;
+      }
+      pl->bwd_cfg_of_m[m] = c;
+    }
     std::vector<char> used(kNumCfg32, 0);
     for (int64_t r = 0; r < b.n_reads; ++r) used[pl->bwd_cfg_of_m[ro[r + 1] - ro[r]]] = 1;
     for (int c = 0; c < kNumCfg32; ++c)

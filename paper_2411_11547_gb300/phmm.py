@@ -53,6 +53,8 @@ class Options(ctypes.Structure):
         ("warps_per_block", ctypes.c_int32),
         ("bin_rows", ctypes.c_int32 * (PHMM_MAX_READ_LEN // 4 + 1)),
         ("bin_table_valid", ctypes.c_int32), ("adjoint_rescue", ctypes.c_int32),
+        ("bwd_rows", ctypes.c_int32 * (PHMM_MAX_READ_LEN // 4 + 1)),
+        ("bwd_table_valid", ctypes.c_int32),
     ]
 
 
@@ -94,6 +96,9 @@ def lib():
             L.phmm_plan_backward_ms.restype = ctypes.c_int
             L.phmm_plan_rescue_counts.argtypes = [vp, vp, vp, i64p]
             L.phmm_plan_rescue_counts.restype = ctypes.c_int
+            L.phmm_autotune.argtypes = [ctypes.POINTER(Batch), ctypes.POINTER(Options),
+                                        ctypes.c_int, ctypes.c_int64, vp]
+            L.phmm_autotune.restype = ctypes.c_int
             L.phmm_probe_pipe.argtypes = [ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]
@@ -103,15 +108,17 @@ def lib():
 
 
 def options(**kw) -> Options:
-    """Library defaults (phmm_options_default) with keyword overrides; `bin_rows` may be a
-    sequence of group ids per 4-row read-length bucket (sets bin_table_valid)."""
+    """Library defaults (phmm_options_default) with keyword overrides; `bin_rows` / `bwd_rows`
+    may be sequences of group ids per 4-row read-length bucket for the forward / adjoint
+    (they set bin_table_valid / bwd_table_valid)."""
     o = Options()
     lib().phmm_options_default(ctypes.byref(o))
     for k, v in kw.items():
-        if k == "bin_rows":
+        if k in ("bin_rows", "bwd_rows"):
+            arr = getattr(o, k)
             for i, x in enumerate(v):
-                o.bin_rows[i] = int(x)
-            o.bin_table_valid = 1
+                arr[i] = int(x)
+            setattr(o, "bin_table_valid" if k == "bin_rows" else "bwd_table_valid", 1)
         else:
             setattr(o, k, int(v))
     return o
@@ -300,6 +307,19 @@ def forward(batch, opts: Options | None = None, device="cuda"):
     plan = Plan(db, opts)
     out, flags = plan.forward()
     return out, flags
+
+
+def autotune(dbatch: DeviceBatch, opts: Options | None = None, which: int = 3,
+             sample_pairs: int = 8192, stream=None) -> Options:
+    """phmm_autotune: measured read-length -> group tables (forward: which & 1, adjoint:
+    which & 2) for this batch, returned in a copy of `opts` (default options if None)."""
+    o = Options.from_buffer_copy(opts if opts is not None else options())
+    b = dbatch.struct()
+    rc = lib().phmm_autotune(ctypes.byref(b), ctypes.byref(o), int(which), int(sample_pairs),
+                             _stream(stream))
+    if rc != PHMM_OK:
+        raise PhmmError(rc, "phmm_autotune")
+    return o
 
 
 def probe_pipe(kind: int, iters: int = 4000):

@@ -72,6 +72,18 @@ def test_forward_rejects_null_plan(lib):
     assert lib.phmm_workspace_bytes(None) == 0
 
 
+def test_autotune_rejects_bad_arguments_on_host(lib):
+    from paper_2411_11547_gb300 import phmm
+    o = phmm.options()
+    b = phmm.Batch()
+    assert lib.phmm_autotune(None, ctypes.byref(o), 3, 16, None) == phmm.PHMM_EINVAL
+    assert lib.phmm_autotune(ctypes.byref(b), None, 3, 16, None) == phmm.PHMM_EINVAL
+    assert lib.phmm_autotune(ctypes.byref(b), ctypes.byref(o), 0, 16, None) == phmm.PHMM_EINVAL
+    assert lib.phmm_autotune(ctypes.byref(b), ctypes.byref(o), 3, 0, None) == phmm.PHMM_EINVAL
+    assert lib.phmm_autotune(ctypes.byref(b), ctypes.byref(o), 3, 16, None) == phmm.PHMM_EINVAL
+    assert o.bin_table_valid == 0 and o.bwd_table_valid == 0
+
+
 def test_autograd_wrapper_checks_tensor_layout():
     import numpy as np
     import torch

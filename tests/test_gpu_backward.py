@@ -152,3 +152,19 @@ def test_autograd_function(phmm):
     grad_close(iq.grad.cpu().numpy(), wi, "d/diq")
     grad_close(dq.grad.cpu().numpy(), wd, "d/ddq")
     assert abs(float(gcp.grad) - wg) <= RTOL * abs(wg) + 1e-9
+
+
+BWD_SHAPES = [(L, K) for L in (4, 8, 16, 32) for K in (4, 6, 8, 10, 12)] + [(32, 16)]
+
+
+@pytest.mark.parametrize("L,K", BWD_SHAPES)
+def test_every_backward_shape(phmm, L, K):
+    # every built adjoint group, forced by a backward table; reads from 1 row up to capacity
+    import torch
+    cap = L * K
+    b = synth.random_pairs(300 + cap + K, 24, (max(1, cap // 3), cap), (1, 260), related=0.6,
+                           qual_dtype=np.float32)
+    assert np.diff(b["read_off"]).max() <= cap
+    c = {4: 0, 8: 1, 16: 2, 32: 3}[L] * 9 + (K - 4) // 2
+    dy = np.random.default_rng(cap).uniform(-1, 1, len(b["pair_read"]))
+    check_against_oracle(phmm, b, dy, bwd_rows=[c] * 129)
