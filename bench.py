@@ -179,6 +179,8 @@ def main():
                     choices=("c4_persistent", "c1_batched", "c3_grad"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="use the built-in group tables instead of phmm_autotune's")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -211,7 +213,20 @@ def main():
     cells = synth.cells(batch)
     P = len(batch["pair_read"])
     dbatch = phmm.DeviceBatch(batch, dev)
-    plan = phmm.Plan(dbatch, phmm.options())
+    # measured read-length -> group tables for this workload shape (outside the timed region,
+    # like plan creation)
+    t_tune = time.perf_counter()
+    opts = phmm.options() if args.no_tune else phmm.autotune(dbatch, which=3, sample_pairs=8192)
+    torch.cuda.synchronize()
+    t_tune = time.perf_counter() - t_tune
+
+    def opts_with(**kw):
+        o = phmm.Options.from_buffer_copy(opts)
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return o
+
+    plan = phmm.Plan(dbatch, opts)
     stream = torch.cuda.current_stream()
     dL = torch.ones(P, dtype=torch.float64, device=dev)
     out, flags = plan.forward()
@@ -255,7 +270,7 @@ def main():
     sample_clk = clocks.stop()
 
     # per-kernel times of the forward from an event-instrumented (non-graph) plan
-    plan_t = phmm.Plan(dbatch, phmm.options(use_graph=0))
+    plan_t = phmm.Plan(dbatch, opts_with(use_graph=0))
     plan_t.forward()
     wf_ms, resc_ms = [], []
     for _ in range(args.steps):
@@ -320,7 +335,7 @@ def main():
                 setattr(db, k, hb[k].to(dev, non_blocking=True))
             db.gcp = float(batch["gcp"])
             db.alpha_mode = 0
-            pl = phmm.Plan(db, phmm.options())
+            pl = phmm.Plan(db, opts)
             o, _ = pl.forward()
             gb, gi, gd, gg = pl.backward(dL)
             out_h.copy_(o, non_blocking=True)
@@ -374,7 +389,10 @@ def main():
         "config": {"workload": f"{args.workload}: {WORKLOAD_DESC[args.workload]}",
                    "pairs": P * ws, "cells": total_cells, "step": "forward + adjoint",
                    "first_line": "FP32 with per-lane exponents (FP64 rescue when unrepresentable)",
-                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"weak x{ws}"},
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"weak x{ws}",
+                   "group_tables": ("built-in" if args.no_tune else
+                                    f"phmm_autotune (8192-pair samples per 16-row read-length "
+                                    f"range, {t_tune:.2f} s, outside the timed region)")},
         "fwd_gcups": fwd_gcups,
         "fwd_wavefront_gcups": cells / (wf * 1e-3) / 1e9,
         "fwd_rescue_ms": statistics.median(resc_ms),

@@ -176,7 +176,9 @@ int phmm_plan_backward_ms(phmm_plan *plan, float *ms_adjoint, float *ms_reduce);
  * Rescue statistics of the latest calls on this plan and workspace, copied to the host
  * (waits for `stream`): counts[0] pairs the forward recomputed in FP64, counts[1] of those
  * that went on to the per-lane-exponent FP64 kernel, counts[2] pairs whose adjoint was
- * finished in FP64, counts[3] reserved (0).
+ * finished in FP64, counts[3] / counts[4] of those handed off because forward and adjoint
+ * mass lay beyond one FP32 exponent range / because a partial sum was not finite, and
+ * counts[5] reserved (0).  counts holds 6 values.
  */
 int phmm_plan_rescue_counts(phmm_plan *plan, const void *ws, void *stream, int64_t *counts);
 

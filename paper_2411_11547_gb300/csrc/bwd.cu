@@ -21,11 +21,15 @@
 // owns K rows, walks the columns from right to left, and exchanges the top row's u and I^
 // with the lane above by __shfl_down_sync.  Forward values are recomputed, not stored:
 //   phase A  runs the per-lane-exponent FP32 forward and checkpoints every lane's register
-//            state at each renormalisation point (every step of the ramp, then every kSeg
-//            steps) into a per-warp scratch slot (streaming stores);
+//            state at each renormalisation point (every step of the ramp, then every
+//            segment of 2..8 steps) into a per-warp scratch slot (streaming stores);
 //   phase B  for each segment, last to first: restores the checkpoint, recomputes the
-//            segment while recording the lane's rows (M, I, D/zeta) after each step
-//            (L2-resident), then runs the adjoint over the segment in reverse.
+//            segment while recording the lane's rows after each step in the warp's shared
+//            memory (M and D/zeta per row and the top row's I; the reverse step rebuilds
+//            the other rows' I with Eq. 2), then runs the adjoint over the segment in
+//            reverse.  Step records never leave the SM: written to global memory they
+//            would move ~2.5 words per cell each way through the SM's L2 port, which
+//            bounds the recompute well below the forward's arithmetic rate.
 // Adjoints carry their own per-lane power-of-two exponent and the inverse of the forward's
 // per-row bias, so a forward x adjoint product is a posterior-scale number times
 // 2^-(E_fwd + E_adj).  The partial sums are held at the lane's current scale and re-based
@@ -85,9 +89,7 @@ int bwd_cfg_supported(int cfg) {
 }
 
 static size_t bwd_smem(int K, int elem, int block) {
-  const int vw = 16 / elem, KV = (K + vw - 1) / vw * vw, units = KV / vw;
-  const int LS = (units % 2 == 1) ? KV : KV + vw;
-  return (size_t)(block / 32) * kCodes * 32 * LS * elem;
+  return (size_t)(block / 32) * bwd_warp_bytes(K, elem);
 }
 
 // Read length -> FP32 backward group (rows per lane <= 12 keeps the adjoint in registers).
@@ -109,16 +111,16 @@ static int blocks_per_sm(BwdKernel k, size_t smem, int block) {
   return nb < 1 ? 1 : nb;
 }
 
-static int64_t bwd_nchk(int L, int64_t n_max) {
-  const int64_t steps = n_max + L - 1 + kSeg;
+// Checkpoints per pair group: one per ramp step, then one per segment.
+static int64_t bwd_nchk(int L, int K, int elem, int64_t n_max) {
+  const int seg = bwd_seg_len(K, elem);
+  const int64_t steps = n_max + L - 1 + seg;
   const int64_t ramp = (L + 15) & ~15;
-  return ramp + (steps + kSeg - 1) / kSeg + 2;
+  return ramp + (steps + seg - 1) / seg + 2;
 }
 
 static int64_t slot_elems(int L, int K, int elem, int64_t n_max) {
-  const int vw = 16 / elem;
-  const int ckw = (3 * K + 4 + vw - 1) / vw * vw, cbw = (3 * K + vw - 1) / vw * vw;
-  return bwd_nchk(L, n_max) * 32 * ckw + kSeg * 32 * cbw;
+  return bwd_nchk(L, K, elem, n_max) * 32 * ck_w(K, elem);
 }
 
 struct BwdLayout {
@@ -247,7 +249,7 @@ int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, floa
       c.f.offset_dev = grp_begin + cfg;
       c.f.count_dev = grp_count + cfg;
       c.f.counter = (int32_t *)(ws + plan_layout_bin(pl, 7)) + cfg;
-      c.nchk = (int32_t)bwd_nchk(L, nmax);
+      c.nchk = (int32_t)bwd_nchk(L, K, 4, nmax);
       c.slot_elems = slot_elems(L, K, 4, nmax);
       c.rescue = o.adjoint_rescue ? 0 : 1;  // without the FP64 pass, failures write NaN
       BwdKernel k = bwd_kernel32(L, K);
@@ -266,7 +268,7 @@ int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, floa
       c.f.offset_dev = nullptr;
       c.f.count_dev = rcnt + k64;
       c.f.counter = rctr + k64;
-      c.nchk = (int32_t)bwd_nchk(32, nmax);
+      c.nchk = (int32_t)bwd_nchk(32, K, 8, nmax);
       c.slot_elems = slot_elems(32, K, 8, nmax);
       c.rescue = 1;
       BwdKernel kk = bwd_kernel64(K);

@@ -24,22 +24,47 @@ struct BwdArgs {
   int32_t *why;                   // [2]: hand-offs for the scale range / non-finite partials
 };
 
-// Steps per recomputed segment (after the ramp): the per-warp record buffer holds kSeg steps,
-// small enough that the records of all resident warps stay in L2.
-constexpr int kSeg = 8;
-
-// Record widths (elements, multiples of the 16-byte vector) of a checkpoint (K rows of M, I,
-// D plus the boundary values, the conversion factor and the exponent) and of a recorded step
-// (K rows of M, I, D).
-template <typename T>
-__host__ __device__ constexpr int vec_w() { return 16 / (int)sizeof(T); }
-template <typename T>
-__host__ __device__ constexpr int ck_width(int K) {
-  return (3 * K + 4 + vec_w<T>() - 1) / vec_w<T>() * vec_w<T>();
+// Widths (elements, multiples of the 16-byte vector) of a checkpoint (K rows of M, I, D/zeta
+// plus the boundary values, the conversion factor and the exponent) and of a step record (K
+// rows of M and D/zeta plus the top row's I: the other rows' I follow from Eq. 2 again).
+__host__ __device__ constexpr int vecw(int elem) { return 16 / elem; }
+__host__ __device__ constexpr int ck_w(int K, int elem) {
+  return (3 * K + 4 + vecw(elem) - 1) / vecw(elem) * vecw(elem);
+}
+__host__ __device__ constexpr int rec_w(int K, int elem) {
+  return (2 * K + 1 + vecw(elem) - 1) / vecw(elem) * vecw(elem);
 }
 template <typename T>
-__host__ __device__ constexpr int rec_width(int K) {
-  return (3 * K + vec_w<T>() - 1) / vec_w<T>() * vec_w<T>();
+__host__ __device__ constexpr int ck_width(int K) { return ck_w(K, (int)sizeof(T)); }
+template <typename T>
+__host__ __device__ constexpr int rec_width(int K) { return rec_w(K, (int)sizeof(T)); }
+
+// Shared memory of one warp: the emission table (kCodes planes of 32 lanes x LS, as
+// TableGeom) and the step records of one segment.  The segment length follows from what fits
+// next to the table at the occupancy the registers allow (warps per SM): 2 to 8 steps.
+__host__ __device__ constexpr int bwd_warps_per_sm(int K, int elem) {
+  return elem == 8 ? 4 : (K <= 4 ? 16 : (K <= 8 ? 12 : 8));
+}
+__host__ __device__ constexpr size_t bwd_table_bytes(int K, int elem) {
+  return (size_t)kCodes * 32 * elem *
+         (((K + vecw(elem) - 1) / vecw(elem)) % 2 == 1
+              ? (K + vecw(elem) - 1) / vecw(elem) * vecw(elem)
+              : (K + vecw(elem) - 1) / vecw(elem) * vecw(elem) + vecw(elem));
+}
+__host__ __device__ constexpr size_t bwd_rec_bytes(int K, int elem) {
+  return (size_t)32 * rec_w(K, elem) * elem;
+}
+// Step records that fit next to the table (the last step of a segment needs none: its state
+// is still in registers), so a segment is one step longer.
+__host__ __device__ constexpr int bwd_rec_fit(int K, int elem) {
+  return (int)(((size_t)227 * 1024 / bwd_warps_per_sm(K, elem) - 256 - bwd_table_bytes(K, elem)) /
+               bwd_rec_bytes(K, elem));
+}
+__host__ __device__ constexpr int bwd_seg_len(int K, int elem) {
+  return bwd_rec_fit(K, elem) + 1 > 8 ? 8 : (bwd_rec_fit(K, elem) + 1 < 2 ? 2 : bwd_rec_fit(K, elem) + 1);
+}
+__host__ __device__ constexpr size_t bwd_warp_bytes(int K, int elem) {
+  return bwd_table_bytes(K, elem) + (size_t)(bwd_seg_len(K, elem) - 1) * bwd_rec_bytes(K, elem);
 }
 
 // Records are stored as [record][16-byte group][lane], so one warp-wide 128-bit access
@@ -84,6 +109,11 @@ __device__ __forceinline__ void rec_load(const T *base, int lane, T (&v)[W]) {
       v[2 * g + 1] = x.y;
     }
   }
+}
+
+// Ask the copy engine to bring `bytes` (a multiple of 16, 16-byte aligned) into L2.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 // Small integers (exponents, base codes) ride in the records as exact floating values.
@@ -152,7 +182,7 @@ __device__ __forceinline__ void adj_rescale(AdjState<T, K> &as, int t, T S, int 
 // state, adjoints, coefficients, five partial sums) grow with the rows per lane.
 template <typename T, int K>
 constexpr int bwd_min_blocks() {
-  return sizeof(T) == 8 ? 1 : (K <= 6 ? 4 : (K <= 8 ? 3 : 2));
+  return sizeof(T) == 8 ? 1 : (K <= 4 ? 4 : (K <= 8 ? 3 : 2));
 }
 
 template <typename T, int L, int K>
@@ -161,6 +191,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
   constexpr int G = 32 / L, VW = G_::VW, LS = G_::LS, CS = G_::CS;
   constexpr int kBias = 2;
   constexpr int CKW = ck_width<T>(K), RW = rec_width<T>(K);
+  constexpr int kSeg = bwd_seg_len(K, sizeof(T));
   // Range of the posterior scale exponent h = E_fwd + E_adj over which the raw products of
   // stored forward and adjoint values are accumulated: below kHmin a product is at most
   // 2^(16 + kHmin) of a posterior (dropped); above kHmax the products a lane needs can fall
@@ -173,12 +204,15 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int t = lane % L, sub = lane / L;
-  // one table per warp: signed emissions beta * lambda (+ for a match, - for a mismatch)
-  T *tblE = reinterpret_cast<T *>(smem_raw) + (size_t)warp * kCodes * CS + lane * LS;
+  // per warp: the table of signed emissions beta * lambda (+ for a match, - for a mismatch)
+  // and the segment's step records
+  static_assert(bwd_table_bytes(K, sizeof(T)) == (size_t)kCodes * CS * sizeof(T), "table");
+  unsigned char *wsm = smem_raw + (size_t)warp * bwd_warp_bytes(K, sizeof(T));
+  T *tblE = reinterpret_cast<T *>(wsm) + lane * LS;
+  T *recS = reinterpret_cast<T *>(wsm + bwd_table_bytes(K, sizeof(T)));
   const int wpb = blockDim.x >> 5;
   T *slot = reinterpret_cast<T *>(a.scratch) + (size_t)(blockIdx.x * wpb + warp) * a.slot_elems;
   T *ckb = slot;
-  T *cbb = slot + (size_t)a.nchk * 32 * CKW;
   const T eps = sizeof(T) == 4 ? (T)fa.eps32 : (T)fa.eps64;
   const T beta = sizeof(T) == 4 ? (T)fa.beta32 : (T)fa.beta64;
 
@@ -373,6 +407,8 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
         st.f = ck[3 * K + 2];
         st.E = bits_int<T>(ck[3 * K + 3]);
       }
+      // bring the next (left) segment's checkpoint from DRAM towards L2 while this one runs
+      if (q > 0 && lane == 0) prefetch_l2(ckb + (size_t)(q - 1) * 32 * CKW, 32 * CKW * sizeof(T));
       st.c = hap_code_at(fa.hcode, hs, n, (int64_t)b - t);
       T mxF = fmax(st.Md, st.Sd);
 #pragma unroll
@@ -387,16 +423,18 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
         T in3[3];
         wf_step<T, L, K, true, true, true>(st, cu, t, bnd, eps, tblE, ap, dl, zt, ei, in3);
         codes |= st.c << (3 * u2);
-        T rec[RW];
+        if (u2 < len - 1) {  // the last step's state stays in registers
+          T rec[RW];
 #pragma unroll
-        for (int r = 0; r < K; ++r) {
-          rec[r] = st.M[r];
-          rec[K + r] = st.I[r];
-          rec[2 * K + r] = st.D[r];
+          for (int r = 0; r < K; ++r) {
+            rec[r] = st.M[r];
+            rec[K + r] = st.D[r];
+          }
+          rec[2 * K] = st.I[0];
+#pragma unroll
+          for (int k = 2 * K + 1; k < RW; ++k) rec[k] = 0;
+          rec_store<T, RW>(recS + (size_t)u2 * 32 * RW, lane, rec);
         }
-#pragma unroll
-        for (int k = 3 * K; k < RW; ++k) rec[k] = 0;
-        rec_store<T, RW>(cbb + (size_t)u2 * 32 * RW, lane, rec);
       }
       const int EF = st.E;
       const T fS = bndS * Num<T>::exp2i(-EF);  // lane 0's boundary row in its own scale
@@ -407,8 +445,27 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
       for (int u2 = len - 1; u2 >= 0; --u2) {
         const int64_t j = (int64_t)b + u2 + 1 - t;  // this lane's column at this step
         const int c = (codes >> (3 * u2)) & 7;
-        T rec[RW];
-        rec_load<T, RW>(cbb + (size_t)u2 * 32 * RW, lane, rec);
+        // forward values of the lane's rows at column j: M, I, D/zeta (rec[r], [K+r], [2K+r])
+        T rec[3 * K];
+        if (u2 == len - 1) {
+#pragma unroll
+          for (int r = 0; r < K; ++r) {
+            rec[r] = st.M[r];
+            rec[K + r] = st.I[r];
+            rec[2 * K + r] = st.D[r];
+          }
+        } else {
+          T sr[RW];
+          rec_load<T, RW>(recS + (size_t)u2 * 32 * RW, lane, sr);
+#pragma unroll
+          for (int r = 0; r < K; ++r) {
+            rec[r] = sr[r];
+            rec[2 * K + r] = sr[K + r];
+          }
+          rec[K] = sr[2 * K];
+#pragma unroll
+          for (int r = 1; r < K; ++r) rec[K + r] = dl[r] * rec[r - 1] + ei[r] * rec[K + r - 1];
+        }
         T e[K];
         load_rows<T, K>(tblE + c * CS, e);
         T rU = __shfl_down_sync(FULL, as.u[0], 1, L);

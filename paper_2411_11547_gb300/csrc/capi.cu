@@ -180,7 +180,7 @@ static void make_layout(phmm_plan *pl) {
   o += 4 * kNumCfg64;
   L.xcnt = o;
   o += 4 * kNumCfg64;
-  L.why = o;  // adjoint hand-off reasons: scale range, non-finite partial, forward failed
+  L.why = o;  // adjoint hand-offs for the scale range / non-finite partials
   o += 4 * 4;
   o = align256(o);
   L.zero_bytes = o - L.zero;
@@ -575,8 +575,9 @@ int phmm_plan_rescue_counts(phmm_plan *pl, const void *ws, void *stream, int64_t
   CK(cudaMemcpyAsync(h + 3 * kNumCfg64, w + pl->L.why, 16, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   counts[0] = counts[1] = counts[2] = 0;
-  // counts[3]: hand-offs for the scale range, times 2^20 plus non-finite partials
-  counts[3] = ((int64_t)h[3 * kNumCfg64] << 20) + h[3 * kNumCfg64 + 1];
+  counts[3] = h[3 * kNumCfg64];      // adjoint hand-offs for the scale range
+  counts[4] = h[3 * kNumCfg64 + 1];  // adjoint hand-offs for non-finite partials
+  counts[5] = 0;
   for (int k = 0; k < kNumCfg64; ++k) {
     counts[0] += h[k];
     counts[1] += h[kNumCfg64 + k];

@@ -281,13 +281,14 @@ class Plan:
         return a.value, r.value
 
     def rescue_counts(self, stream=None):
-        """(forward FP64 rescues, of which extended, adjoint FP64 hand-offs) of the last calls."""
-        c = (ctypes.c_int64 * 4)()
+        """(forward FP64 rescues, of which extended, adjoint FP64 hand-offs, of which for the
+        scale range, of which for non-finite partials, 0)."""
+        c = (ctypes.c_int64 * 6)()
         rc = lib().phmm_plan_rescue_counts(self.handle, ctypes.c_void_p(self._ws_ptr),
                                            _stream(stream), c)
         if rc != PHMM_OK:
             raise PhmmError(rc, "phmm_plan_rescue_counts")
-        return int(c[0]), int(c[1]), int(c[2]), int(c[3]) >> 20, int(c[3]) & 0xfffff
+        return tuple(int(x) for x in c)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -49,7 +49,7 @@ def run_grad(ph, batch, dy, **opt):
 
 
 def check_against_oracle(ph, b, dy, **opt):
-    y, gb, gi, gd, gg, _ = run_grad(ph, b, dy, **opt)
+    y, gb, gi, gd, gg, plan = run_grad(ph, b, dy, **opt)
     wy, wb, wi, wd, wg = oracle.backward_batch(b, dy)
     grad_close(gb, wb, "d/dbq")
     grad_close(gi, wi, "d/diq")
