@@ -532,11 +532,12 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
             const T eiB = r == K - 1 ? eib : ei[r + 1];
             const T add = r == K - 1 ? sd : (T)0;
             const T uba = fabs(ub);       // u(r+1, j+1); u carries the emission's sign
-            const T Il = eiB * Ibl;       // eps x I^(r+1, j)
             const T zD = zt[r] * as.Db[r];
             const T Mv = rec[r], Iv = rec[K + r], Dv = rec[2 * K + r];  // forward, column j
             const T Mb = apB * uba + dlB * Ibl + zD + add;               // M^(r, j)
-            const T Ib = uba + Il + add;                                 // I^(r, j)
+            // I^(r, j): one FMA on the row-to-row chain; eps x I^(r+1, j) again for the partial
+            const T Ib = fma(eiB, Ibl, uba + add);
+            const T Il = eiB * Ibl;
             const T Dn = uba + eps * as.Db[r];                           // D^(r, j)
             const T un = e[r] * Mb;                                      // u(r, j)
             if constexpr (PROD) {

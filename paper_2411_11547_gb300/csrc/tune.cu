@@ -193,7 +193,12 @@ static float time_candidate(const SubBatch &sb, const phmm_options &opt, int whi
     };
     ok = ok && phmm_forward(plan, w, wsb, (double *)out, (uint8_t *)flags, s) == PHMM_OK &&
          run() == PHMM_OK;  // warm-up (graph capture, caches)
-    const int reps = which == 1 ? 3 : 2;
+    // one timed call sets the repetitions: at least ~10 ms of timed work per candidate
+    int reps = 1;
+    float ms1 = 0.f;
+    ok = ok && !cudaEventRecord(e0, s) && run() == PHMM_OK && !cudaEventRecord(e1, s) &&
+         !cudaEventSynchronize(e1) && !cudaEventElapsedTime(&ms1, e0, e1);
+    if (ok) reps = std::max(2, std::min(50, (int)(10.f / std::max(ms1, 1e-3f)) + 1));
     ok = ok && !cudaEventRecord(e0, s);
     for (int i = 0; ok && i < reps; ++i) ok = run() == PHMM_OK;
     ok = ok && !cudaEventRecord(e1, s) && !cudaEventSynchronize(e1) &&

@@ -311,7 +311,7 @@ def forward(batch, opts: Options | None = None, device="cuda"):
 
 
 def autotune(dbatch: DeviceBatch, opts: Options | None = None, which: int = 3,
-             sample_pairs: int = 8192, stream=None) -> Options:
+             sample_pairs: int = 32768, stream=None) -> Options:
     """phmm_autotune: measured read-length -> group tables (forward: which & 1, adjoint:
     which & 2) for this batch, returned in a copy of `opts` (default options if None)."""
     o = Options.from_buffer_copy(opts if opts is not None else options())
