@@ -38,12 +38,16 @@ extern "C" {
 /* ---- status codes ---------------------------------------------------------------- */
 #define PHMM_OK 0
 #define PHMM_EINVAL -1   /* bad argument: offsets, lengths, bases, quals, gcp, pair ids */
-#define PHMM_ETOOLONG -2 /* a read longer than PHMM_MAX_READ_LEN */
+#define PHMM_ETOOLONG -2 /* a read longer than the call supports */
 #define PHMM_ENOMEM -3   /* workspace smaller than phmm_workspace_bytes() */
 #define PHMM_ECUDA -4    /* a CUDA runtime call failed; see phmm_last_cuda_error() */
 #define PHMM_ESTATE -5   /* call out of order (e.g. backward on a plan never run forward) */
 
 #define PHMM_MAX_READ_LEN 512 /* longest read (rows) one wavefront group holds */
+/* Longest read phmm_forward scores: reads beyond PHMM_MAX_READ_LEN are swept in row tiles of
+ * PHMM_MAX_READ_LEN rows (Sec. III-C supports reads up to 1,024).  phmm_backward and
+ * phmm_forward_noalloc take reads up to PHMM_MAX_READ_LEN only. */
+#define PHMM_MAX_READ_LEN_FWD 2048
 
 /* ---- per-pair flags written by phmm_forward ---------------------------------------- */
 #define PHMM_FLAG_FP32 1       /* result from the FP32 wavefront (|err| <= 1e-3 log10) */
@@ -112,8 +116,9 @@ typedef struct phmm_plan phmm_plan;
  * it (the only host synchronisation of the library): read and haplotype offsets must be
  * non-decreasing from 0, every read and haplotype non-empty, bases in {A,C,G,T,N} (either
  * case), Phred values finite-or-+inf and >= 0 with delta+zeta <= 1 (alpha_mode 0), pair ids
- * in range, gcp > 0.  Returns PHMM_EINVAL / PHMM_ETOOLONG on bad input (no plan is
- * created), PHMM_OK otherwise with *plan set.  The plan keeps the batch pointers.
+ * in range, gcp > 0, reads at most PHMM_MAX_READ_LEN_FWD long.  Returns PHMM_EINVAL /
+ * PHMM_ETOOLONG on bad input (no plan is created), PHMM_OK otherwise with *plan set.  The
+ * plan keeps the batch pointers.
  */
 int phmm_plan_create(const phmm_batch *batch, const phmm_options *opt, void *stream,
                      phmm_plan **plan);
@@ -141,7 +146,8 @@ int phmm_forward(phmm_plan *plan, void *ws, size_t ws_bytes, double *out_log10,
  *                                pairs that share each read (overwritten, FP64-accumulated);
  *   d_gcp                      : device double [1], d(loss)/d(gcp) summed over all pairs.
  * Invalid pairs contribute nothing.  Requires a preceding phmm_forward with the same plan and
- * ws (PHMM_ESTATE otherwise).  Asynchronous on `stream`.
+ * ws (PHMM_ESTATE otherwise).  Reads longer than PHMM_MAX_READ_LEN (row tiles) have no
+ * adjoint: a plan holding one returns PHMM_ETOOLONG.  Asynchronous on `stream`.
  */
 int phmm_backward(phmm_plan *plan, void *ws, size_t ws_bytes, const double *dL,
                   float *d_base_q, float *d_ins_q, float *d_del_q, double *d_gcp,

@@ -122,6 +122,7 @@ static int default_cfg_of_m(int m) {
 using namespace phmm;
 
 struct WsLayout {
+  size_t tile = 0;  // row-tile buffers (plans holding reads longer than one group)
   size_t rp, rcode, hcode, key, order, zero, zero_bytes, counts, ctr32, ctr64, ctrx, rcnt, xcnt,
       offsets, cursor, grp_begin, grp_count, rlist, xlist, bwd, total, why;
 };
@@ -190,6 +191,18 @@ static void make_layout(phmm_plan *pl) {
   L.grp_count = take(4 * kNumCfg32);
   L.rlist = take((size_t)4 * P * kNumCfg64);
   L.xlist = take((size_t)4 * P * kNumCfg64);
+  if (pl->max_m > PHMM_MAX_READ_LEN) {
+    // 2 buffers of n_max columns (32 B each, enough for FP64) per resident warp of the widest
+    // persistent launch of the 32 x 16 group (FP32 or FP64, either tier)
+    const int block = 32 * pl->o.warps_per_block, c16 = cfg_index(32, 16);
+    int bps = 1;
+    for (int e = 0; e < 2; ++e) {
+      bps = std::max(bps, fwd32_blocks_per_sm(c16, e == 1, block));
+      bps = std::max(bps, fwd64_blocks_per_sm(2, e == 1, block));
+    }
+    const size_t warps = (size_t)pl->sms * bps * (block / 32);
+    L.tile = take(warps * 2 * (size_t)pl->n_max * 32);
+  }
   L.bwd = o;
   L.total = o;
 }
@@ -265,7 +278,7 @@ int phmm_plan_create(const phmm_batch *batch, const phmm_options *opt, void *str
   for (int64_t r = 0; r < b.n_reads; ++r) {
     const int64_t m = ro[r + 1] - ro[r];
     if (m <= 0) return PHMM_EINVAL;
-    if (m > PHMM_MAX_READ_LEN) return PHMM_ETOOLONG;
+    if (m > PHMM_MAX_READ_LEN_FWD) return PHMM_ETOOLONG;
     max_m = std::max<int>(max_m, (int)m);
   }
   for (int64_t h = 0; h < b.n_haps; ++h)
@@ -310,7 +323,8 @@ int phmm_plan_create(const phmm_batch *batch, const phmm_options *opt, void *str
   }
   if (o.binning) {
     std::vector<char> used(kNumCfg32, 0);
-    for (int64_t r = 0; r < b.n_reads; ++r) used[pl->cfg_of_m[ro[r + 1] - ro[r]]] = 1;
+    for (int64_t r = 0; r < b.n_reads; ++r)
+      used[pl->cfg_of_m[std::min<int64_t>(ro[r + 1] - ro[r], PHMM_MAX_READ_LEN)]] = 1;
     for (int c = 0; c < kNumCfg32; ++c)
       if (used[c]) pl->used_cfgs.push_back(c);
   }
@@ -324,7 +338,8 @@ int phmm_plan_create(const phmm_batch *batch, const phmm_options *opt, void *str
       pl->bwd_cfg_of_m[m] = c;
     }
     std::vector<char> used(kNumCfg32, 0);
-    for (int64_t r = 0; r < b.n_reads; ++r) used[pl->bwd_cfg_of_m[ro[r + 1] - ro[r]]] = 1;
+    for (int64_t r = 0; r < b.n_reads; ++r)
+      used[pl->bwd_cfg_of_m[std::min<int64_t>(ro[r + 1] - ro[r], PHMM_MAX_READ_LEN)]] = 1;
     for (int c = 0; c < kNumCfg32; ++c)
       if (used[c]) pl->bwd_used.push_back(c);
   }
@@ -416,6 +431,8 @@ static int enqueue_forward(phmm_plan *pl, char *ws, double *out, uint8_t *flags,
     a.rescue_list[k] = (int32_t *)(ws + L.rlist) + (size_t)k * std::max<int64_t>(b.n_pairs, 1);
   }
   a.rescue_count = rcnt;
+  a.tilebuf = pl->L.tile ? (void *)(ws + L.tile) : nullptr;
+  a.tile_cols = pl->n_max;
   const bool ext = o.first_line == PHMM_FIRST_EXT32;
   a.mode = ext ? 1 : 0;
   const int block = 32 * o.warps_per_block;
@@ -448,6 +465,7 @@ static int enqueue_forward(phmm_plan *pl, char *ws, double *out, uint8_t *flags,
         grid = pl->sms * std::max(1, fwd32_blocks_per_sm(cfg, ext, block));
       } else {
         grid = (int)((items + o.warps_per_block - 1) / o.warps_per_block);
+        c.tilebuf = nullptr;  // buffers exist per resident warp of persistent launches only
       }
       rc = launch_fwd32(cfg, ext, grid, block, s, c);
       if (rc) return cuda_fail((cudaError_t)rc);
@@ -532,6 +550,7 @@ int phmm_backward(phmm_plan *pl, void *ws, size_t ws_bytes, const double *dL, fl
   if (pl->b.n_pairs > 0 && !dL) return PHMM_EINVAL;
   if (((uintptr_t)ws & 255) != 0) return PHMM_EINVAL;
   if (ws_bytes < pl->L.total) return PHMM_ENOMEM;
+  if (pl->max_m > PHMM_MAX_READ_LEN) return PHMM_ETOOLONG;  // row tiles have no adjoint
   if (!pl->fwd_done) return PHMM_ESTATE;
   (void)cudaGetLastError();
   int launches = 0;

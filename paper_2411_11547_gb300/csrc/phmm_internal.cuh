@@ -72,6 +72,8 @@ struct FwdArgs {
   double eps64, beta64;
   int32_t mode;             // 0 plain32, 1 ext32, 2 plain64, 3 ext64
   int32_t rescue;           // 1: append failures to rescue lists, 0: write whatever results
+  void *tilebuf;            // row tiles: 2 x tile_cols TileCol<T> per resident warp (or null)
+  int64_t tile_cols;        // columns per tile buffer (the longest haplotype)
 };
 
 // Launchers (one per precision); return cudaError_t of the launch.

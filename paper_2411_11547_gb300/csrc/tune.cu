@@ -241,7 +241,7 @@ extern "C" int phmm_autotune(const phmm_batch *batch, phmm_options *opt, int whi
   std::vector<std::vector<int64_t>> members(kRanges);
   for (int64_t p = 0; p < b.n_pairs; ++p) {
     const int64_t m = ro[pr[p] + 1] - ro[pr[p]];
-    members[(m - 1) / kRange].push_back(p);
+    if (m <= PHMM_MAX_READ_LEN) members[(m - 1) / kRange].push_back(p);  // longer: row tiles
   }
   phmm_options work = *opt;  // ranges without pairs keep the caller's entries
   for (int k = 0; k < kRanges; ++k) {

@@ -144,6 +144,13 @@ __device__ __forceinline__ void row_params(const FwdArgs &a, int64_t g, T &ap, T
   }
 }
 
+// One column of a row tile's last row, handed to the next tile (E: the last lane's
+// exponent, an exact small integer in T).
+template <typename T>
+struct alignas(16) TileCol {
+  T M, I, X, E;
+};
+
 // Register state of one lane of the wavefront.
 template <typename T, int K>
 struct WfState {
@@ -166,10 +173,14 @@ struct WfState {
 // (in3[2] then holds I + D, not D).
 // ABS_E: the table holds signed emissions (the sign marks a match, for the adjoint); the
 // recurrence uses their magnitudes (a free operand modifier).
-template <typename T, int L, int K, bool EXT, bool PRIMED = false, bool ABS_E = false>
+// TOP: lane 0 takes the row above its strip from (tM, tI, tT), already in its own scale,
+// instead of the DP's row 0 (row tiles of long reads: the previous tile's last row).
+template <typename T, int L, int K, bool EXT, bool PRIMED = false, bool ABS_E = false,
+          bool TOP = false>
 __device__ __forceinline__ void wf_step(WfState<T, K> &st, int cu, int t, T bnd, T eps,
                                         const T *tbl, const T (&ap)[K], const T (&dl)[K],
-                                        const T (&zt)[K], const T (&ei)[K], T (&in3)[3]) {
+                                        const T (&zt)[K], const T (&ei)[K], T (&in3)[3],
+                                        T tM = 0, T tI = 0, T tT = 0) {
   constexpr unsigned FULL = 0xffffffffu;
   constexpr int CS = TableGeom<T, K>::CS;
   const int cin = __shfl_up_sync(FULL, st.c, 1, L);
@@ -179,14 +190,21 @@ __device__ __forceinline__ void wf_step(WfState<T, K> &st, int cu, int t, T bnd,
   T inI = __shfl_up_sync(FULL, st.I[K - 1], 1, L);
   T inD = __shfl_up_sync(FULL, third, 1, L);
   if (t == 0) {  // row 0 (or the last pad row): M = 0, I + D = K0 * D(0, j) carried in I
-    inM = 0;
-    inI = bnd;
-    inD = PRIMED ? bnd : (T)0;
+    if constexpr (TOP) {
+      inM = tM;
+      inI = tI;
+      inD = tT;
+    } else {
+      inM = 0;
+      inI = bnd;
+      inD = PRIMED ? bnd : (T)0;
+    }
   }
   if constexpr (EXT) {
-    inM *= st.f;
-    inI *= st.f;
-    inD *= st.f;
+    const T fe = (TOP && t == 0) ? (T)1 : st.f;
+    inM *= fe;
+    inI *= fe;
+    inD *= fe;
   }
   in3[0] = inM;
   in3[1] = inI;
@@ -301,7 +319,10 @@ __global__ void __launch_bounds__(128, wf_min_blocks<T, K>()) wf_forward(const F
         m = (int)(a.read_off[ri + 1] - r0);
         hs = hap_start(a.hap_off[hi], hi);
         n = a.hap_off[hi + 1] - a.hap_off[hi];
-        if (m <= 0 || m > L * K || n <= 0) bad = true;
+        // reads longer than the group only in row tiles (32 x 16 group, buffer present)
+        const bool tiles_ok = L == 32 && K == 16 && a.tilebuf != nullptr && n <= a.tile_cols;
+        if (m <= 0 || n <= 0 || (m > L * K && !(tiles_ok && m <= PHMM_MAX_READ_LEN_FWD)))
+          bad = true;
       } else {
         bad = true;
       }
@@ -310,15 +331,34 @@ __global__ void __launch_bounds__(128, wf_min_blocks<T, K>()) wf_forward(const F
         n = 0;
       }
     }
-    const int npad = L * K - m;
+    // Row tiles (Sec. III-C handles reads up to 1,024 bases): the 32 x 16 group scores reads
+    // longer than its 512 rows in tiles of 512 rows, top to bottom.  Each tile sweeps every
+    // column; its last row (M, I and the third value the lane below takes, with the last
+    // lane's exponent) goes column by column to a per-warp buffer, and the next tile's lane 0
+    // reads it as the row above its strip.  The top padding sits in the first tile.
+    constexpr bool TILED = (L == 32 && K == 16);
+    constexpr int LK = L * K;
+    const int ntile = TILED ? ((m + LK - 1) / LK > 1 ? (m + LK - 1) / LK : 1) : 1;
+    const int npad = ntile * LK - m;
     // K0 * D(0, j), carried in I; the per-lane-exponent tier starts from K0 = 1
     const T bnd = n > 0 ? (EXT ? (T)1 : Num<T>::K0) / (T)n : (T)0;
+    constexpr int kBias = EXT ? 2 : 0;
+    TileCol<T> *tb_in = nullptr, *tb_out = nullptr;
+    if constexpr (TILED) {
+      TileCol<T> *tb = reinterpret_cast<TileCol<T> *>(a.tilebuf) +
+                       ((size_t)blockIdx.x * wpb + warp) * 2 * (size_t)a.tile_cols;
+      tb_in = tb;
+      tb_out = tb + a.tile_cols;
+    }
+    T Sfin = 0;
+    int Efin = 0;
+    for (int tile = 0; tile < ntile; ++tile) {
+    const bool last_tile = tile == ntile - 1;
 
     // ---- per-row constants and the emission table ---------------------------------------
     // Per-lane-exponent tier: row r of every lane is stored with an extra factor 2^(kBias*r)
     // (folded exactly into the row's emission, delta and I coefficients), which offsets the
     // typical decay of the forward values down the rows so one exponent covers the lane.
-    constexpr int kBias = EXT ? 2 : 0;
     T ap[K], dl[K], zt[K], ei[K], M[K], I[K], D[K];
 #pragma unroll
     for (int r0v = 0; r0v < K; r0v += VW) {
@@ -331,7 +371,8 @@ __global__ void __launch_bounds__(128, wf_min_blocks<T, K>()) wf_forward(const F
           for (int c = 0; c < kCodes; ++c) ev[c][u] = 0;
           continue;
         }
-        const int pos = t * K + rr - npad;  // 0-based read position; < 0: pad row
+        // 0-based read position; < 0: pad row
+        const int pos = tile * LK + t * K + rr - npad;
         const T bias = rr ? (T)(1 << kBias) : (T)1;
         M[rr] = 0;
         D[rr] = 0;
@@ -367,7 +408,7 @@ __global__ void __launch_bounds__(128, wf_min_blocks<T, K>()) wf_forward(const F
     WfState<T, K> st;
     st.c = kNull;
     st.Md = 0;
-    st.Sd = t == 0 ? bnd : (T)0;
+    st.Sd = (t == 0 && tile == 0) ? bnd : (T)0;
     st.acc = 0;
     st.f = t == 0 ? (T)1 : Num<T>::exp2i(-kBias * (K - 1));
     st.E = 0;
@@ -376,6 +417,16 @@ __global__ void __launch_bounds__(128, wf_min_blocks<T, K>()) wf_forward(const F
       st.M[r] = M[r];
       st.I[r] = I[r];
       st.D[r] = D[r];
+    }
+    if constexpr (TILED && EXT) {
+      // lane 0 of a lower tile starts at the exponent that brings column 1 of the row above
+      // near 1 (its own state is still zero, so this changes nothing else)
+      if (tile > 0 && t == 0 && n > 0) {
+        const TileCol<T> c1 = tb_in[0];
+        const T mx = fmax(c1.M, fmax(c1.I, c1.X));
+        st.E = mx > (T)0 ? (int)c1.E - kBias * (K - 1) + Num<T>::ilog2(mx) : 0;
+        st.f = Num<T>::exp2i(-st.E);
+      }
     }
     const uint4 null16 = make_uint4(0x05050505u, 0x05050505u, 0x05050505u, 0x05050505u);
     // Ramp: the first steps carry the wavefront into every lane; in the per-lane-exponent
@@ -386,18 +437,58 @@ __global__ void __launch_bounds__(128, wf_min_blocks<T, K>()) wf_forward(const F
     // later steps (other pairs of the warp still running) only rescale it by powers of two,
     // which would change the rounding of log10 and make results depend on the packing.
     const int fin = n > 0 ? (int)n + L - 1 : 0;
-    T Sfin = 0;
-    int Efin = 0;
     bool done = false;
     uint4 hv = null16;
+    TileCol<T> cb = {0, 0, 0, 0};  // row above, columns s0+1 .. s0+16 (lane u: column s0+u+1)
+    // one step of the tile at 0-based step s (u: step within the current 16-step chunk)
+    auto step = [&](int s, int u, int code) {
+      T in3[3];
+      if constexpr (TILED) {
+        T tM = 0, tI, tT;
+        if (tile == 0) {
+          tI = EXT ? bnd * st.f : bnd;
+          tT = EXT ? bnd * st.f : (T)0;
+        } else {
+          const T bM = __shfl_sync(FULL, cb.M, u), bI = __shfl_sync(FULL, cb.I, u);
+          const T bX = __shfl_sync(FULL, cb.X, u), bE = __shfl_sync(FULL, cb.E, u);
+          const T cv = EXT ? Num<T>::exp2i((int)bE - st.E - kBias * (K - 1)) : (T)1;
+          tM = bM * cv;
+          tI = bI * cv;
+          tT = bX * cv;
+        }
+        wf_step<T, L, K, EXT, EXT, false, true>(st, code, t, bnd, eps, tbl, ap, dl, zt, ei,
+                                                in3, tM, tI, tT);
+        if (!last_tile && t == L - 1) {
+          const int64_t j = (int64_t)s + 1 - (L - 1);  // the last lane's column
+          if (j >= 1 && j <= n) {
+            TileCol<T> o;
+            o.M = st.M[K - 1];
+            o.I = st.I[K - 1];
+            o.X = EXT ? st.I[K - 1] + zt[K - 1] * st.D[K - 1] : st.D[K - 1];
+            o.E = (T)st.E;
+            tb_out[j - 1] = o;
+          }
+        }
+      } else {
+        wf_step<T, L, K, EXT, EXT>(st, code, t, bnd, eps, tbl, ap, dl, zt, ei, in3);
+      }
+    };
+    auto load_cols = [&](int s0) {
+      if constexpr (TILED) {
+        if (tile > 0) {
+          const int64_t c = (int64_t)s0 + lane;
+          cb = (lane < 16 && c < n) ? tb_in[c] : TileCol<T>{0, 0, 0, 0};
+        }
+      }
+    };
     for (int s = 0; s < ramp; ++s) {
-      if ((s & 15) == 0) hv = (t == 0 && s < n) ? *reinterpret_cast<const uint4 *>(a.hcode + hs + s)
-                                                : null16;
+      if ((s & 15) == 0) {
+        hv = (t == 0 && s < n) ? *reinterpret_cast<const uint4 *>(a.hcode + hs + s) : null16;
+        load_cols(s);
+      }
       const int q = (s >> 2) & 3;
       const uint32_t w = q == 0 ? hv.x : (q == 1 ? hv.y : (q == 2 ? hv.z : hv.w));
-      T in3[3];
-      wf_step<T, L, K, EXT, EXT>(st, (w >> (8 * (s & 3))) & 0xff, t, bnd, eps, tbl, ap, dl, zt,
-                                 ei, in3);
+      step(s, s & 15, (w >> (8 * (s & 3))) & 0xff);
       if (!done && s + 1 >= fin) {
         Sfin = st.acc;
         Efin = st.E;
@@ -407,12 +498,11 @@ __global__ void __launch_bounds__(128, wf_min_blocks<T, K>()) wf_forward(const F
     }
     for (int s0 = ramp; s0 < steps; s0 += 16) {
       hv = (t == 0 && s0 < n) ? *reinterpret_cast<const uint4 *>(a.hcode + hs + s0) : null16;
+      load_cols(s0);
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
         const uint32_t w = u < 4 ? hv.x : (u < 8 ? hv.y : (u < 12 ? hv.z : hv.w));
-        T in3[3];
-        wf_step<T, L, K, EXT, EXT>(st, (w >> (8 * (u & 3))) & 0xff, t, bnd, eps, tbl, ap, dl,
-                                   zt, ei, in3);
+        step(s0 + u, u, (w >> (8 * (u & 3))) & 0xff);
       }
       if (!done && s0 + 16 >= fin) {
         Sfin = st.acc;
@@ -425,6 +515,13 @@ __global__ void __launch_bounds__(128, wf_min_blocks<T, K>()) wf_forward(const F
       Sfin = st.acc;
       Efin = st.E;
     }
+    if constexpr (TILED) {  // this tile's last row becomes the next tile's row above
+      TileCol<T> *x = tb_in;
+      tb_in = tb_out;
+      tb_out = x;
+      __syncwarp();
+    }
+    }  // tiles
     const T acc = Sfin;
     const int E = Efin;
 

@@ -193,7 +193,7 @@ def test_invalid_inputs_are_rejected(phmm):
     bad = dict(b, ins_q=np.zeros_like(b["ins_q"]))  # delta + zeta > 1
     with pytest.raises(phmm.PhmmError):
         phmm.Plan(phmm.DeviceBatch(bad))
-    long = synth.random_pairs(2, 2, (513, 520), (600, 700))
+    long = synth.random_pairs(2, 2, (2049, 2060), (600, 700))
     with pytest.raises(phmm.PhmmError) as e:
         phmm.Plan(phmm.DeviceBatch(long))
     assert e.value.status == phmm.PHMM_ETOOLONG
@@ -218,3 +218,40 @@ def test_c4_sampled_pairs_full_size_launch(phmm):
     idx = np.unique(np.array(idx))
     sb = synth.subset_pairs(b, idx)
     check(got[idx], flags[idx], oracle.forward_batch(sb), phmm)
+
+
+@pytest.mark.parametrize("first_line", [0, 1])
+def test_long_reads_in_row_tiles(phmm, first_line):
+    # reads longer than one group (512 rows) are swept in row tiles of 512, alone and mixed
+    # with short reads in one binned batch; the plain first line sends them through the
+    # tiled FP64 and per-lane-exponent FP64 kernels
+    import torch
+    rng = np.random.default_rng(31)
+    regs = []
+    for m, n in [(513, 700), (600, 40), (1024, 1100), (1500, 300), (2048, 2100), (777, 777),
+                 (1025, 5), (520, 1)]:
+        hap = synth.ACGT[rng.integers(0, 4, n)]
+        if n >= m and rng.random() < 0.7:
+            o = int(rng.integers(0, n - m + 1))
+            read = hap[o:o + m].copy()
+            sub = rng.random(m) < 0.01
+            read[sub] = synth.ACGT[rng.integers(0, 4, int(sub.sum()))]
+        else:
+            read = synth.ACGT[rng.integers(0, 4, m)]
+        regs.append(([hap], [read], [rng.integers(10, 41, m)], [rng.integers(30, 46, m)],
+                     [rng.integers(30, 46, m)]))
+    short = synth.random_pairs(32, 60, (1, 512), (1, 600), related=0.5)
+    b = synth._assemble(regs, 10.0, "long_reads")
+    for k in ("read_bases", "base_q", "ins_q", "del_q", "hap_bases"):
+        b[k] = np.concatenate([b[k], short[k]])
+    b["read_off"] = np.concatenate([b["read_off"], b["read_off"][-1] + short["read_off"][1:]])
+    b["hap_off"] = np.concatenate([b["hap_off"], b["hap_off"][-1] + short["hap_off"][1:]])
+    nr, nh = len(regs), len(regs)
+    b["pair_read"] = np.concatenate([b["pair_read"], short["pair_read"] + nr]).astype(np.int32)
+    b["pair_hap"] = np.concatenate([b["pair_hap"], short["pair_hap"] + nh]).astype(np.int32)
+    got, flags, plan = run(phmm, b, first_line=first_line)
+    check(got, flags, oracle.forward_batch(b), phmm)
+    # the adjoint has no row tiles
+    with pytest.raises(phmm.PhmmError) as e:
+        plan.backward(torch.ones(len(got), dtype=torch.float64, device="cuda"))
+    assert e.value.status == phmm.PHMM_ETOOLONG
