@@ -38,6 +38,10 @@ FWD_OPS_PER_CELL = 6
 # recurrences (u = beta lambda M^: 1; M^: 3; I^: 1; D^: 1) plus the partials (alpha, beta:
 # 2; Q: I+D, alpha' M + S, w M^ G: 3; delta, zeta: 2; eps: 2): 6 + 6 + 9 + 1 = 22.
 BWD_OPS_PER_CELL = 22
+# DRAM bytes per cell of the adjoint kernel (read + written: its checkpoints), from an ncu
+# capture of wf_backward<float,16,10> on the 4.5e9-cell c3_grad batch (10.45 GB read, 13.73 GB
+# written); the c4 step's traffic is this times its cells.
+BWD_DRAM_BYTES_PER_CELL = (10.447 + 13.734) * 1e9 / 4.5e9
 
 WORKLOAD_DESC = {
     "c4_persistent": "65,536 regions x 4 haplotypes x 16 reads = 2^22 pairs; read length "
@@ -411,7 +415,11 @@ def main():
                       "fwd_frac": fwd_wf_achieved / peak,
                       "fwd_ops_per_cell": FWD_OPS_PER_CELL, "bwd_ops_per_cell": BWD_OPS_PER_CELL},
         "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
-                     "unit": "T FP32 lane-ops/s", "frac": achieved / peak, "traffic": None},
+                     "unit": "T FP32 lane-ops/s", "frac": achieved / peak,
+                     "traffic": cells * BWD_DRAM_BYTES_PER_CELL if dom_bwd else None,
+                     "traffic_source": ("ncu dram__bytes_read+write of the adjoint on c3_grad "
+                                        "(5.37 B/cell), scaled by this step's cells"
+                                        if dom_bwd else None)},
         "gpu_launches": launches * args.steps,
         "clocks": sample_clk,
     }

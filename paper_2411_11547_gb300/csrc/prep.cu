@@ -35,10 +35,15 @@ __global__ void k_validate_reads(const uint8_t *bases, const void *bq, const voi
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
        g += (int64_t)gridDim.x * blockDim.x) {
     if (base_code(bases[g]) < 0) e |= kErrBase;
-    const double b = qual_at(bq, qual_f32, g), i = qual_at(iq, qual_f32, g),
-                 d = qual_at(dq, qual_f32, g);
-    if (!(b >= 0.0) || !(i >= 0.0) || !(d >= 0.0)) e |= kErrQual;  // NaN or negative
-    if (alpha_mode == 0 && pow(10.0, -i / 10.0) + pow(10.0, -d / 10.0) > 1.0) e |= kErrAlpha;
+    // uint8 and float32 Phred values are exact in float
+    const float b = (float)qual_at(bq, qual_f32, g), i = (float)qual_at(iq, qual_f32, g),
+                d = (float)qual_at(dq, qual_f32, g);
+    if (!(b >= 0.f) || !(i >= 0.f) || !(d >= 0.f)) e |= kErrQual;  // NaN or negative
+    // delta + zeta <= 1 holds whenever both gap quals are >= 10 log10(2) ~ 3.0103 (each term
+    // <= 1/2); only below that is the exact FP64 test needed (FP64 is slow on this part)
+    if (alpha_mode == 0 && fminf(i, d) < 3.0103f &&
+        pow(10.0, -(double)i / 10.0) + pow(10.0, -(double)d / 10.0) > 1.0)
+      e |= kErrAlpha;
   }
   if (e) atomicOr(err, e);
 }
