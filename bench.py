@@ -362,6 +362,33 @@ def main():
         e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms, "_cells": cells}
 
+    # end-to-end forward scoring from host memory (the host workflow of Sec. III-A) on the
+    # NA12878-shaped stand-in of Table I: pipelined subsets, host packing and copies included
+    hostpipe = None
+    if not args.no_e2e and rank == 0:
+        na = synth.na12878_like()
+        na_cells = synth.cells(na)
+        na_opts = phmm.autotune(phmm.DeviceBatch(na, dev), which=1, sample_pairs=32768)
+        sub_cells = 1 << 34
+        phmm.score_host(na, na_opts, subset_cells=sub_cells)
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            phmm.score_host(na, na_opts, subset_cells=sub_cells)
+            ts.append(time.perf_counter() - t0)
+        t_na = statistics.median(ts)
+        na_in = sum(np.asarray(na[k]).nbytes for k in ("read_bases", "base_q", "ins_q", "del_q",
+                                                       "read_off", "hap_bases", "hap_off",
+                                                       "pair_read", "pair_hap"))
+        hostpipe = {"workload": "na12878_like: 100,000 regions of 1..6 haplotypes (30..521) x "
+                                "2..30 reads (10..151), "
+                                f"{len(na['pair_read'])} pairs, {na_cells} cells",
+                    "call": "phmm_score_host (forward, host arrays in and out)",
+                    "subset_cells": sub_cells, "ms": t_na * 1e3,
+                    "gcups": na_cells / t_na / 1e9, "h2d_bytes": int(na_in),
+                    "d2h_bytes": int(len(na["pair_read"]) * 9)}
+        del na
+
     # max over ranks of the step time
     if dist is not None:
         t = torch.tensor([ms, ms_fwd, e2e["ms_per_step"] if e2e else 0.0], device=dev)
@@ -425,6 +452,8 @@ def main():
     }
     if e2e:
         line["e2e"] = e2e
+    if hostpipe:
+        line["host_pipeline_fwd"] = hostpipe
     if rank == 0 and not args.no_cpu_baseline:
         g, ocells, kp, dt, cores = oracle_sample(batch, 15.0)
         line["cpu_baseline"] = {"value": g, "unit": UNIT, "cores": cores, "kind": "oracle",

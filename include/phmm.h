@@ -207,6 +207,22 @@ int phmm_autotune(const phmm_batch *batch, phmm_options *opt, int which, int64_t
                   void *stream);
 
 /*
+ * End-to-end scoring of a batch held in HOST memory (the host workflow of Sec. III-A:
+ * partition, transfer, score, transfer back).  Every pointer of *host_batch is host memory
+ * (pageable or pinned); out_log10 / out_flags are host arrays of n_pairs.  Pairs are grouped by
+ * read and cut into subsets of about `subset_cells` cells (Eq. 5; at least one read each).
+ * Each subset is packed into pinned staging memory, copied to the device in one transfer,
+ * validated and scored with phmm_plan_create / phmm_forward (options `opt`, NULL = defaults;
+ * CUDA graphs are not used), and its results copied back, on one of two streams, so the host
+ * packing and copies of one subset overlap the scoring of the previous one.  Allocates and
+ * frees its own pinned and device buffers; returns when every result is in host memory.
+ * Errors: those of phmm_plan_create for a subset's inputs, PHMM_ENOMEM if a buffer cannot be
+ * allocated, PHMM_ECUDA.
+ */
+int phmm_score_host(const phmm_batch *host_batch, const phmm_options *opt,
+                    int64_t subset_cells, double *out_log10, uint8_t *out_flags);
+
+/*
  * Forward scoring for callers that cannot allocate device memory.
  *
  * Some callers may not call cudaMalloc at all: code running inside a framework that owns

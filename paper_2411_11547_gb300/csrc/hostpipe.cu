@@ -1,0 +1,225 @@
+// End-to-end scoring of a batch held in host memory: the host workflow of Sec. III-A
+// (partition into subsets, transfer, score, transfer back), with the copies of one subset
+// overlapping the scoring of the previous one.
+//
+// Pairs are grouped by read (every pair of a read in one subset) and cut into subsets of
+// about `subset_cells` cells.  Per subset the host packs the reads, the haplotypes the pairs
+// use (renumbered) and the pairs into one pinned staging buffer, which goes to the device in
+// one copy; the subset is then validated and scored through the library's own plan and
+// forward on one of two streams, and its log10 L and flags come back by one copy each.  While
+// the GPU scores subset k on one stream, the host packs subset k+1 and starts its copy on
+// the other.
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#include "phmm.h"
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+struct Slot {
+  cudaStream_t s = nullptr;
+  unsigned char *stage = nullptr;  // pinned: packed inputs
+  size_t stage_cap = 0;
+  unsigned char *dev = nullptr;    // device: packed inputs, then log10 L and flags
+  size_t dev_cap = 0;
+  void *ws = nullptr;              // device: workspace
+  size_t ws_cap = 0;
+  unsigned char *hres = nullptr;   // pinned: log10 L and flags of the subset
+  size_t hres_cap = 0;
+  phmm_plan *plan = nullptr;
+  std::vector<int64_t> pairs;      // global pair ids of the subset in flight
+  size_t res_off = 0;              // offset of the results in dev / hres
+  bool busy = false;
+};
+
+int grow_pinned(unsigned char **p, size_t *cap, size_t need) {
+  if (need <= *cap) return 0;
+  if (*p) cudaFreeHost(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMallocHost((void **)p, need) != cudaSuccess) return PHMM_ENOMEM;
+  *cap = need;
+  return 0;
+}
+int grow_device(void **p, size_t *cap, size_t need) {
+  if (need <= *cap) return 0;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMalloc(p, need) != cudaSuccess) return PHMM_ENOMEM;
+  *cap = need;
+  return 0;
+}
+
+// Wait for a slot's subset and scatter its results to the caller's arrays.
+int drain(Slot &sl, double *out, uint8_t *flags) {
+  if (!sl.busy) return 0;
+  if (cudaStreamSynchronize(sl.s) != cudaSuccess) return PHMM_ECUDA;
+  const size_t np = sl.pairs.size();
+  const double *r = (const double *)sl.hres;
+  const uint8_t *f = (const uint8_t *)(sl.hres + up(8 * np));
+  for (size_t i = 0; i < np; ++i) {
+    out[sl.pairs[i]] = r[i];
+    flags[sl.pairs[i]] = f[i];
+  }
+  phmm_plan_destroy(sl.plan);
+  sl.plan = nullptr;
+  sl.busy = false;
+  return 0;
+}
+
+}  // namespace
+
+extern "C" int phmm_score_host(const phmm_batch *hb, const phmm_options *opt,
+                               int64_t subset_cells, double *out_log10, uint8_t *out_flags) {
+  if (!hb || !out_log10 || !out_flags || subset_cells < 1) return PHMM_EINVAL;
+  const phmm_batch &b = *hb;
+  if (b.n_reads < 1 || b.n_haps < 1 || b.n_pairs < 0) return PHMM_EINVAL;
+  if (!b.read_bases || !b.base_q || !b.ins_q || !b.del_q || !b.read_off || !b.hap_bases ||
+      !b.hap_off || (b.n_pairs > 0 && (!b.pair_read || !b.pair_hap)))
+    return PHMM_EINVAL;
+  if (b.n_pairs == 0) return PHMM_OK;
+  const int64_t R = b.n_reads, H = b.n_haps, P = b.n_pairs;
+  const int64_t *ro = b.read_off, *ho = b.hap_off;
+  if (ro[0] != 0 || ho[0] != 0) return PHMM_EINVAL;
+  for (int64_t r = 0; r < R; ++r)
+    if (ro[r + 1] <= ro[r]) return PHMM_EINVAL;
+  for (int64_t h = 0; h < H; ++h)
+    if (ho[h + 1] <= ho[h]) return PHMM_EINVAL;
+  // pairs grouped by read (counting sort)
+  std::vector<int64_t> rptr(R + 1, 0), rpairs(P);
+  for (int64_t p = 0; p < P; ++p) {
+    const int32_t r = b.pair_read[p], h = b.pair_hap[p];
+    if (r < 0 || r >= R || h < 0 || h >= H) return PHMM_EINVAL;
+    ++rptr[r + 1];
+  }
+  for (int64_t r = 0; r < R; ++r) rptr[r + 1] += rptr[r];
+  {
+    std::vector<int64_t> cur(rptr.begin(), rptr.end() - 1);
+    for (int64_t p = 0; p < P; ++p) rpairs[cur[b.pair_read[p]]++] = p;
+  }
+  phmm_options o;
+  if (opt) o = *opt; else phmm_options_default(&o);
+  o.use_graph = 0;  // one forward per plan: no graph to replay
+  const int qe = b.qual_dtype == PHMM_QUAL_F32 ? 4 : 1;
+
+  Slot slot[2];
+  int rc = 0;
+  for (auto &sl : slot)
+    if (cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking) != cudaSuccess) rc = PHMM_ECUDA;
+  std::vector<int64_t> hmark(H, -1);
+  std::vector<int32_t> hmap(H, 0);
+  int64_t lo = 0, k = 0;
+  while (rc == 0 && lo < R) {
+    // the next subset: whole reads up to about subset_cells cells
+    int64_t hi = lo, cells = 0;
+    while (hi < R && (hi == lo || cells < subset_cells)) {
+      const int64_t m = ro[hi + 1] - ro[hi];
+      for (int64_t i = rptr[hi]; i < rptr[hi + 1]; ++i) {
+        const int32_t h = b.pair_hap[rpairs[i]];
+        cells += m * (ho[h + 1] - ho[h]);
+      }
+      ++hi;
+    }
+    Slot &sl = slot[k & 1];
+    if ((rc = drain(sl, out_log10, out_flags))) break;
+    // the subset's pairs, haplotypes (renumbered in first-use order) and sizes
+    sl.pairs.assign(rpairs.begin() + rptr[lo], rpairs.begin() + rptr[hi]);
+    const int64_t np = (int64_t)sl.pairs.size(), nr = hi - lo;
+    std::vector<int32_t> haps;
+    int64_t sn = 0;
+    for (int64_t p : sl.pairs) {
+      const int32_t h = b.pair_hap[p];
+      if (hmark[h] != k) {
+        hmark[h] = k;
+        hmap[h] = (int32_t)haps.size();
+        haps.push_back(h);
+        sn += ho[h + 1] - ho[h];
+      }
+    }
+    const int64_t nh = (int64_t)haps.size();
+    const int64_t sm = ro[hi] - ro[lo];
+    // packed layout: bases, 3 quals, read offsets, haplotype bases and offsets, pair ids
+    size_t off[9], tot = 0;
+    const size_t sz[9] = {(size_t)sm, (size_t)sm * qe, (size_t)sm * qe, (size_t)sm * qe,
+                          (size_t)(nr + 1) * 8, (size_t)sn, (size_t)(nh + 1) * 8,
+                          (size_t)np * 4, (size_t)np * 4};
+    for (int i = 0; i < 9; ++i) {
+      off[i] = tot;
+      tot += up(sz[i]);
+    }
+    sl.res_off = tot;
+    const size_t res = up(8 * (size_t)np) + up((size_t)np);
+    if ((rc = grow_pinned(&sl.stage, &sl.stage_cap, tot))) break;
+    if ((rc = grow_pinned(&sl.hres, &sl.hres_cap, res))) break;
+    if ((rc = grow_device((void **)&sl.dev, &sl.dev_cap, tot + res))) break;
+    unsigned char *st = sl.stage;
+    std::memcpy(st + off[0], b.read_bases + ro[lo], sm);
+    std::memcpy(st + off[1], (const unsigned char *)b.base_q + ro[lo] * qe, sm * qe);
+    std::memcpy(st + off[2], (const unsigned char *)b.ins_q + ro[lo] * qe, sm * qe);
+    std::memcpy(st + off[3], (const unsigned char *)b.del_q + ro[lo] * qe, sm * qe);
+    int64_t *sro = (int64_t *)(st + off[4]);
+    for (int64_t r = 0; r <= nr; ++r) sro[r] = ro[lo + r] - ro[lo];
+    int64_t *sho = (int64_t *)(st + off[6]);
+    sho[0] = 0;
+    for (int64_t i = 0; i < nh; ++i) {
+      const int32_t h = haps[i];
+      const int64_t n = ho[h + 1] - ho[h];
+      std::memcpy(st + off[5] + sho[i], b.hap_bases + ho[h], n);
+      sho[i + 1] = sho[i] + n;
+    }
+    int32_t *spr = (int32_t *)(st + off[7]), *sph = (int32_t *)(st + off[8]);
+    for (int64_t i = 0; i < np; ++i) {
+      spr[i] = (int32_t)(b.pair_read[sl.pairs[i]] - lo);
+      sph[i] = hmap[b.pair_hap[sl.pairs[i]]];
+    }
+    if (cudaMemcpyAsync(sl.dev, st, tot, cudaMemcpyHostToDevice, sl.s) != cudaSuccess) {
+      rc = PHMM_ECUDA;
+      break;
+    }
+    phmm_batch d = b;
+    d.n_reads = nr;
+    d.n_haps = nh;
+    d.n_pairs = np;
+    d.read_bases = sl.dev + off[0];
+    d.base_q = sl.dev + off[1];
+    d.ins_q = sl.dev + off[2];
+    d.del_q = sl.dev + off[3];
+    d.read_off = (const int64_t *)(sl.dev + off[4]);
+    d.hap_bases = sl.dev + off[5];
+    d.hap_off = (const int64_t *)(sl.dev + off[6]);
+    d.pair_read = (const int32_t *)(sl.dev + off[7]);
+    d.pair_hap = (const int32_t *)(sl.dev + off[8]);
+    // validation waits for this stream only: the other stream's subset keeps the GPU busy
+    if ((rc = phmm_plan_create(&d, &o, sl.s, &sl.plan))) break;
+    const size_t wsb = phmm_workspace_bytes(sl.plan);
+    if ((rc = grow_device(&sl.ws, &sl.ws_cap, wsb + 256))) break;
+    double *dout = (double *)(sl.dev + sl.res_off);
+    uint8_t *dfl = (uint8_t *)(sl.dev + sl.res_off + up(8 * (size_t)np));
+    if ((rc = phmm_forward(sl.plan, sl.ws, wsb, dout, dfl, sl.s))) break;
+    if (cudaMemcpyAsync(sl.hres, sl.dev + sl.res_off, res, cudaMemcpyDeviceToHost, sl.s) !=
+        cudaSuccess) {
+      rc = PHMM_ECUDA;
+      break;
+    }
+    sl.busy = true;
+    lo = hi;
+    ++k;
+  }
+  for (auto &sl : slot) {
+    const int r2 = rc ? (cudaStreamSynchronize(sl.s), 0) : drain(sl, out_log10, out_flags);
+    if (!rc) rc = r2;
+    if (sl.plan) phmm_plan_destroy(sl.plan);
+    if (sl.stage) cudaFreeHost(sl.stage);
+    if (sl.hres) cudaFreeHost(sl.hres);
+    if (sl.dev) cudaFree(sl.dev);
+    if (sl.ws) cudaFree(sl.ws);
+    if (sl.s) cudaStreamDestroy(sl.s);
+  }
+  return rc;
+}

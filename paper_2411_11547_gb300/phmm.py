@@ -99,6 +99,9 @@ def lib():
             L.phmm_autotune.argtypes = [ctypes.POINTER(Batch), ctypes.POINTER(Options),
                                         ctypes.c_int, ctypes.c_int64, vp]
             L.phmm_autotune.restype = ctypes.c_int
+            L.phmm_score_host.argtypes = [ctypes.POINTER(Batch), ctypes.POINTER(Options),
+                                          ctypes.c_int64, vp, vp]
+            L.phmm_score_host.restype = ctypes.c_int
             L.phmm_probe_pipe.argtypes = [ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]
@@ -321,6 +324,48 @@ def autotune(dbatch: DeviceBatch, opts: Options | None = None, which: int = 3,
     if rc != PHMM_OK:
         raise PhmmError(rc, "phmm_autotune")
     return o
+
+
+def host_batch_struct(batch, keep):
+    """Batch struct over host numpy arrays (kept alive in `keep`)."""
+    def arr(k, dt):
+        a = np.ascontiguousarray(batch[k], dtype=dt)
+        keep.append(a)
+        return a.ctypes.data
+    qd = np.asarray(batch["base_q"]).dtype
+    qdt = np.float32 if qd == np.float32 else np.uint8
+    b = Batch()
+    b.n_reads = len(batch["read_off"]) - 1
+    b.n_haps = len(batch["hap_off"]) - 1
+    b.n_pairs = len(batch["pair_read"])
+    b.read_bases = arr("read_bases", np.uint8)
+    b.base_q = arr("base_q", qdt)
+    b.ins_q = arr("ins_q", qdt)
+    b.del_q = arr("del_q", qdt)
+    b.qual_dtype = QUAL_F32 if qdt == np.float32 else QUAL_U8
+    b.alpha_mode = int(batch.get("alpha_mode", 0))
+    b.read_off = arr("read_off", np.int64)
+    b.hap_bases = arr("hap_bases", np.uint8)
+    b.hap_off = arr("hap_off", np.int64)
+    b.pair_read = arr("pair_read", np.int32)
+    b.pair_hap = arr("pair_hap", np.int32)
+    b.gcp = float(batch["gcp"])
+    return b
+
+
+def score_host(batch, opts: Options | None = None, subset_cells: int = 1 << 33):
+    """phmm_score_host: log10 L and flags (numpy) of a batch held in host memory, scored in
+    pipelined subsets of about `subset_cells` cells."""
+    keep = []
+    b = host_batch_struct(batch, keep)
+    P = b.n_pairs
+    out = np.empty(P, dtype=np.float64)
+    flags = np.empty(P, dtype=np.uint8)
+    rc = lib().phmm_score_host(ctypes.byref(b), ctypes.byref(opts) if opts is not None else None,
+                               int(subset_cells), out.ctypes.data, flags.ctypes.data)
+    if rc != PHMM_OK:
+        raise PhmmError(rc, "phmm_score_host")
+    return out, flags
 
 
 def probe_pipe(kind: int, iters: int = 4000):

@@ -293,9 +293,37 @@ def c4_persistent(seed=4, regions=65536, n_haps=4, n_reads=16):
                  lambda k: np.full(k, 45), 10.0, "c4_persistent")
 
 
+def na12878_like(seed=5, regions=100_000):
+    """Stand-in for the end-to-end scoring workload of Table I (NA12878: 55.1 M pairs in
+    998,837 batches, reads 10..151 with mean 58, haplotypes 30..521): per region 1..6
+    haplotypes and 2..30 reads (about 55 pairs per region), read length log-uniform 10..151,
+    haplotype length log-uniform 30..521 with each region's first haplotype at least as long
+    as its longest read; quals as C1.  100,000 regions is about a tenth of the dataset."""
+    rng = np.random.default_rng(seed)
+    nh = rng.integers(1, 7, size=regions)
+    nr = rng.integers(2, 31, size=regions)
+    hap_region = np.repeat(np.arange(regions), nh)
+    read_region = np.repeat(np.arange(regions), nr)
+    rl = np.minimum(_log_uniform_int(rng, 10, 151, int(nr.sum())), 151)
+    hl = np.minimum(_log_uniform_int(rng, 30, 521, int(nh.sum())), 521)
+    maxr = np.zeros(regions, dtype=np.int64)
+    np.maximum.at(maxr, read_region, rl)
+    first = np.concatenate([[0], np.cumsum(nh)[:-1]])
+    hl[first] = np.maximum(hl[first], maxr)
+
+    def bq(k):
+        lo = rng.random(k) < 0.2
+        return np.where(lo, rng.integers(2, 16, size=k), rng.integers(25, 41, size=k))
+
+    return _bulk(rng, hl, hap_region, rl, read_region, regions, bq,
+                 lambda k: rng.integers(30, 46, size=k), lambda k: rng.integers(30, 46, size=k),
+                 10.0, "na12878_like")
+
+
 def make(name: str, **kw):
     return {"c0_plain": c0_plain, "c1_batched": c1_batched, "c2_stress": c2_stress,
-            "c3_grad": c3_grad, "c4_persistent": c4_persistent}[name](**kw)
+            "c3_grad": c3_grad, "c4_persistent": c4_persistent,
+            "na12878_like": na12878_like}[name](**kw)
 
 
 def subset_pairs(batch, idx):

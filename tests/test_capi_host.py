@@ -105,3 +105,21 @@ def test_autograd_wrapper_checks_tensor_layout():
                                     layout["read_off"].int(), layout["hap_bases"],
                                     layout["hap_off"], layout["pair_read"], layout["pair_hap"],
                                     b["gcp"])
+
+
+def test_score_host_rejects_bad_input_before_touching_the_gpu(lib):
+    import numpy as np
+    from paper_2411_11547_gb300 import phmm, synth
+    b = synth.random_pairs(4, 6, (5, 10), (5, 10))
+    keep = []
+    s = phmm.host_batch_struct(b, keep)
+    out = np.empty(6)
+    fl = np.empty(6, dtype=np.uint8)
+    assert lib.phmm_score_host(None, None, 10, out.ctypes.data, fl.ctypes.data) == phmm.PHMM_EINVAL
+    assert lib.phmm_score_host(ctypes.byref(s), None, 0, out.ctypes.data,
+                               fl.ctypes.data) == phmm.PHMM_EINVAL
+    bad = dict(b, pair_hap=b["pair_hap"].copy())
+    bad["pair_hap"][2] = 99
+    s2 = phmm.host_batch_struct(bad, keep)
+    assert lib.phmm_score_host(ctypes.byref(s2), None, 10, out.ctypes.data,
+                               fl.ctypes.data) == phmm.PHMM_EINVAL
