@@ -369,7 +369,7 @@ def main():
         na = synth.na12878_like()
         na_cells = synth.cells(na)
         na_opts = phmm.autotune(phmm.DeviceBatch(na, dev), which=1, sample_pairs=32768)
-        sub_cells = 1 << 34
+        sub_cells = 1 << 33
         phmm.score_host(na, na_opts, subset_cells=sub_cells)
         ts = []
         for _ in range(3):

@@ -214,13 +214,16 @@ int phmm_autotune(const phmm_batch *batch, phmm_options *opt, int which, int64_t
  * Each subset is packed into pinned staging memory, copied to the device in one transfer,
  * validated and scored with phmm_plan_create / phmm_forward (options `opt`, NULL = defaults;
  * CUDA graphs are not used), and its results copied back, on one of two streams, so the host
- * packing and copies of one subset overlap the scoring of the previous one.  Allocates and
- * frees its own pinned and device buffers; returns when every result is in host memory.
- * Errors: those of phmm_plan_create for a subset's inputs, PHMM_ENOMEM if a buffer cannot be
- * allocated, PHMM_ECUDA.
+ * packing and copies of one subset overlap the scoring of the previous one.  Returns when
+ * every result is in host memory.  Its pinned staging and device buffers grow to the largest
+ * subset seen and are kept for later calls on the same device (pinned allocation is slow);
+ * phmm_score_host_release() frees them.  Calls are serialised by a lock.  Errors: those of
+ * phmm_plan_create for a subset's inputs, PHMM_ENOMEM if a buffer cannot be allocated,
+ * PHMM_ECUDA (buffers are then freed).
  */
 int phmm_score_host(const phmm_batch *host_batch, const phmm_options *opt,
                     int64_t subset_cells, double *out_log10, uint8_t *out_flags);
+void phmm_score_host_release(void);
 
 /*
  * Forward scoring for callers that cannot allocate device memory.

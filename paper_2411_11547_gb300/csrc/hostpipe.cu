@@ -13,6 +13,8 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
+#include <thread>
 #include <vector>
 #include "phmm.h"
 
@@ -32,10 +34,30 @@ struct Slot {
   unsigned char *hres = nullptr;   // pinned: log10 L and flags of the subset
   size_t hres_cap = 0;
   phmm_plan *plan = nullptr;
-  std::vector<int64_t> pairs;      // global pair ids of the subset in flight
+  std::vector<int64_t> pairs;      // global pair ids of the subset in flight (if scattered)
+  bool contiguous = false;         // else: the pairs are p0 .. p0 + np - 1
+  int64_t p0 = 0, np = 0;
   size_t res_off = 0;              // offset of the results in dev / hres
   bool busy = false;
 };
+
+// memcpy split over host threads (large copies only)
+void par_copy(void *dst, const void *src, size_t bytes) {
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const size_t T = std::min<size_t>({(size_t)hw, (size_t)16, bytes / (4u << 20) + 1});
+  if (T <= 1) {
+    std::memcpy(dst, src, bytes);
+    return;
+  }
+  std::vector<std::thread> th;
+  const size_t chunk = (bytes + T - 1) / T;
+  for (size_t i = 0; i < T; ++i) {
+    const size_t a = i * chunk, b = std::min(bytes, a + chunk);
+    if (a < b)
+      th.emplace_back([=] { std::memcpy((char *)dst + a, (const char *)src + a, b - a); });
+  }
+  for (auto &t : th) t.join();
+}
 
 int grow_pinned(unsigned char **p, size_t *cap, size_t need) {
   if (need <= *cap) return 0;
@@ -60,12 +82,17 @@ int grow_device(void **p, size_t *cap, size_t need) {
 int drain(Slot &sl, double *out, uint8_t *flags) {
   if (!sl.busy) return 0;
   if (cudaStreamSynchronize(sl.s) != cudaSuccess) return PHMM_ECUDA;
-  const size_t np = sl.pairs.size();
+  const size_t np = (size_t)sl.np;
   const double *r = (const double *)sl.hres;
   const uint8_t *f = (const uint8_t *)(sl.hres + up(8 * np));
-  for (size_t i = 0; i < np; ++i) {
-    out[sl.pairs[i]] = r[i];
-    flags[sl.pairs[i]] = f[i];
+  if (sl.contiguous) {
+    par_copy(out + sl.p0, r, 8 * np);
+    std::memcpy(flags + sl.p0, f, np);
+  } else {
+    for (size_t i = 0; i < np; ++i) {
+      out[sl.pairs[i]] = r[i];
+      flags[sl.pairs[i]] = f[i];
+    }
   }
   phmm_plan_destroy(sl.plan);
   sl.plan = nullptr;
@@ -73,7 +100,36 @@ int drain(Slot &sl, double *out, uint8_t *flags) {
   return 0;
 }
 
+// Staging and device buffers kept between calls (pinned allocations are slow to make), for
+// the device they were made on; one call at a time uses them.
+struct Cache {
+  std::mutex mu;
+  int device = -1;
+  Slot slot[2];
+};
+Cache &cache() {
+  static Cache c;
+  return c;
+}
+void release_slots(Slot (&slot)[2]) {
+  for (auto &sl : slot) {
+    if (sl.stage) cudaFreeHost(sl.stage);
+    if (sl.hres) cudaFreeHost(sl.hres);
+    if (sl.dev) cudaFree(sl.dev);
+    if (sl.ws) cudaFree(sl.ws);
+    if (sl.s) cudaStreamDestroy(sl.s);
+    sl = Slot();
+  }
+}
+
 }  // namespace
+
+extern "C" void phmm_score_host_release(void) {
+  Cache &c = cache();
+  std::lock_guard<std::mutex> lock(c.mu);
+  release_slots(c.slot);
+  c.device = -1;
+}
 
 extern "C" int phmm_score_host(const phmm_batch *hb, const phmm_options *opt,
                                int64_t subset_cells, double *out_log10, uint8_t *out_flags) {
@@ -91,27 +147,41 @@ extern "C" int phmm_score_host(const phmm_batch *hb, const phmm_options *opt,
     if (ro[r + 1] <= ro[r]) return PHMM_EINVAL;
   for (int64_t h = 0; h < H; ++h)
     if (ho[h + 1] <= ho[h]) return PHMM_EINVAL;
-  // pairs grouped by read (counting sort)
-  std::vector<int64_t> rptr(R + 1, 0), rpairs(P);
+  // pairs grouped by read: already so when pair_read is non-decreasing (all-vs-all batches
+  // list a read's pairs together), else by a counting sort
+  std::vector<int64_t> rptr(R + 1, 0), rpairs;
+  bool sorted = true;
   for (int64_t p = 0; p < P; ++p) {
     const int32_t r = b.pair_read[p], h = b.pair_hap[p];
     if (r < 0 || r >= R || h < 0 || h >= H) return PHMM_EINVAL;
     ++rptr[r + 1];
+    if (p && r < b.pair_read[p - 1]) sorted = false;
   }
   for (int64_t r = 0; r < R; ++r) rptr[r + 1] += rptr[r];
-  {
+  if (!sorted) {
+    rpairs.resize(P);
     std::vector<int64_t> cur(rptr.begin(), rptr.end() - 1);
     for (int64_t p = 0; p < P; ++p) rpairs[cur[b.pair_read[p]]++] = p;
   }
+  auto pair_at = [&](int64_t i) { return sorted ? i : rpairs[i]; };
   phmm_options o;
   if (opt) o = *opt; else phmm_options_default(&o);
   o.use_graph = 0;  // one forward per plan: no graph to replay
   const int qe = b.qual_dtype == PHMM_QUAL_F32 ? 4 : 1;
 
-  Slot slot[2];
+  Cache &cc = cache();
+  std::lock_guard<std::mutex> lock(cc.mu);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PHMM_ECUDA;
+  if (cc.device != dev) {  // buffers of another device: start afresh
+    release_slots(cc.slot);
+    cc.device = dev;
+  }
+  Slot(&slot)[2] = cc.slot;
   int rc = 0;
   for (auto &sl : slot)
-    if (cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking) != cudaSuccess) rc = PHMM_ECUDA;
+    if (!sl.s && cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking) != cudaSuccess)
+      rc = PHMM_ECUDA;
   std::vector<int64_t> hmark(H, -1);
   std::vector<int32_t> hmap(H, 0);
   int64_t lo = 0, k = 0;
@@ -121,28 +191,47 @@ extern "C" int phmm_score_host(const phmm_batch *hb, const phmm_options *opt,
     while (hi < R && (hi == lo || cells < subset_cells)) {
       const int64_t m = ro[hi + 1] - ro[hi];
       for (int64_t i = rptr[hi]; i < rptr[hi + 1]; ++i) {
-        const int32_t h = b.pair_hap[rpairs[i]];
+        const int32_t h = b.pair_hap[pair_at(i)];
         cells += m * (ho[h + 1] - ho[h]);
       }
       ++hi;
     }
     Slot &sl = slot[k & 1];
     if ((rc = drain(sl, out_log10, out_flags))) break;
-    // the subset's pairs, haplotypes (renumbered in first-use order) and sizes
-    sl.pairs.assign(rpairs.begin() + rptr[lo], rpairs.begin() + rptr[hi]);
-    const int64_t np = (int64_t)sl.pairs.size(), nr = hi - lo;
+    // the subset's pairs and haplotypes.  Fast path: the pairs are one contiguous range and
+    // the haplotypes they use fill most of one contiguous range [hmin, hmax], which is then
+    // copied whole and renumbered by offset; otherwise haplotypes are renumbered in
+    // first-use order and gathered one by one.
+    const int64_t p0 = rptr[lo], np = rptr[hi] - rptr[lo], nr = hi - lo;
+    sl.contiguous = sorted;
+    sl.p0 = p0;
+    if (sorted) sl.pairs.clear();
+    else sl.pairs.assign(rpairs.begin() + p0, rpairs.begin() + rptr[hi]);
+    sl.np = np;
+    int32_t hmin = INT32_MAX, hmax = -1;
+    for (int64_t i = 0; i < np; ++i) {
+      const int32_t h = b.pair_hap[pair_at(p0 + i)];
+      hmin = std::min(hmin, h);
+      hmax = std::max(hmax, h);
+    }
     std::vector<int32_t> haps;
     int64_t sn = 0;
-    for (int64_t p : sl.pairs) {
-      const int32_t h = b.pair_hap[p];
-      if (hmark[h] != k) {
-        hmark[h] = k;
-        hmap[h] = (int32_t)haps.size();
-        haps.push_back(h);
-        sn += ho[h + 1] - ho[h];
+    bool hrange = false;
+    if ((int64_t)(hmax - hmin + 1) <= 2 * np + 16) {
+      hrange = true;
+      sn = ho[hmax + 1] - ho[hmin];
+    } else {
+      for (int64_t i = 0; i < np; ++i) {
+        const int32_t h = b.pair_hap[pair_at(p0 + i)];
+        if (hmark[h] != k) {
+          hmark[h] = k;
+          hmap[h] = (int32_t)haps.size();
+          haps.push_back(h);
+          sn += ho[h + 1] - ho[h];
+        }
       }
     }
-    const int64_t nh = (int64_t)haps.size();
+    const int64_t nh = hrange ? (int64_t)(hmax - hmin + 1) : (int64_t)haps.size();
     const int64_t sm = ro[hi] - ro[lo];
     // packed layout: bases, 3 quals, read offsets, haplotype bases and offsets, pair ids
     size_t off[9], tot = 0;
@@ -159,24 +248,30 @@ extern "C" int phmm_score_host(const phmm_batch *hb, const phmm_options *opt,
     if ((rc = grow_pinned(&sl.hres, &sl.hres_cap, res))) break;
     if ((rc = grow_device((void **)&sl.dev, &sl.dev_cap, tot + res))) break;
     unsigned char *st = sl.stage;
-    std::memcpy(st + off[0], b.read_bases + ro[lo], sm);
-    std::memcpy(st + off[1], (const unsigned char *)b.base_q + ro[lo] * qe, sm * qe);
-    std::memcpy(st + off[2], (const unsigned char *)b.ins_q + ro[lo] * qe, sm * qe);
-    std::memcpy(st + off[3], (const unsigned char *)b.del_q + ro[lo] * qe, sm * qe);
+    par_copy(st + off[0], b.read_bases + ro[lo], sm);
+    par_copy(st + off[1], (const unsigned char *)b.base_q + ro[lo] * qe, sm * qe);
+    par_copy(st + off[2], (const unsigned char *)b.ins_q + ro[lo] * qe, sm * qe);
+    par_copy(st + off[3], (const unsigned char *)b.del_q + ro[lo] * qe, sm * qe);
     int64_t *sro = (int64_t *)(st + off[4]);
     for (int64_t r = 0; r <= nr; ++r) sro[r] = ro[lo + r] - ro[lo];
     int64_t *sho = (int64_t *)(st + off[6]);
     sho[0] = 0;
-    for (int64_t i = 0; i < nh; ++i) {
-      const int32_t h = haps[i];
-      const int64_t n = ho[h + 1] - ho[h];
-      std::memcpy(st + off[5] + sho[i], b.hap_bases + ho[h], n);
-      sho[i + 1] = sho[i] + n;
+    if (hrange) {
+      par_copy(st + off[5], b.hap_bases + ho[hmin], sn);
+      for (int64_t i = 0; i <= nh; ++i) sho[i] = ho[hmin + i] - ho[hmin];
+    } else {
+      for (int64_t i = 0; i < nh; ++i) {
+        const int32_t h = haps[i];
+        const int64_t n = ho[h + 1] - ho[h];
+        std::memcpy(st + off[5] + sho[i], b.hap_bases + ho[h], n);
+        sho[i + 1] = sho[i] + n;
+      }
     }
     int32_t *spr = (int32_t *)(st + off[7]), *sph = (int32_t *)(st + off[8]);
     for (int64_t i = 0; i < np; ++i) {
-      spr[i] = (int32_t)(b.pair_read[sl.pairs[i]] - lo);
-      sph[i] = hmap[b.pair_hap[sl.pairs[i]]];
+      const int64_t p = pair_at(p0 + i);
+      spr[i] = (int32_t)(b.pair_read[p] - lo);
+      sph[i] = hrange ? b.pair_hap[p] - hmin : hmap[b.pair_hap[p]];
     }
     if (cudaMemcpyAsync(sl.dev, st, tot, cudaMemcpyHostToDevice, sl.s) != cudaSuccess) {
       rc = PHMM_ECUDA;
@@ -215,11 +310,12 @@ extern "C" int phmm_score_host(const phmm_batch *hb, const phmm_options *opt,
     const int r2 = rc ? (cudaStreamSynchronize(sl.s), 0) : drain(sl, out_log10, out_flags);
     if (!rc) rc = r2;
     if (sl.plan) phmm_plan_destroy(sl.plan);
-    if (sl.stage) cudaFreeHost(sl.stage);
-    if (sl.hres) cudaFreeHost(sl.hres);
-    if (sl.dev) cudaFree(sl.dev);
-    if (sl.ws) cudaFree(sl.ws);
-    if (sl.s) cudaStreamDestroy(sl.s);
+    sl.plan = nullptr;
+    sl.busy = false;
+  }
+  if (rc) {  // after an error, give the buffers back
+    release_slots(slot);
+    cc.device = -1;
   }
   return rc;
 }

@@ -102,6 +102,8 @@ def lib():
             L.phmm_score_host.argtypes = [ctypes.POINTER(Batch), ctypes.POINTER(Options),
                                           ctypes.c_int64, vp, vp]
             L.phmm_score_host.restype = ctypes.c_int
+            L.phmm_score_host_release.argtypes = []
+            L.phmm_score_host_release.restype = None
             L.phmm_probe_pipe.argtypes = [ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]
