@@ -168,3 +168,32 @@ def test_every_backward_shape(phmm, L, K):
     c = {4: 0, 8: 1, 16: 2, 32: 3}[L] * 9 + (K - 4) // 2
     dy = np.random.default_rng(cap).uniform(-1, 1, len(b["pair_read"]))
     check_against_oracle(phmm, b, dy, bwd_rows=[c] * 129)
+
+
+def test_c4_adjoint_full_size_sampled_regions(phmm):
+    """The adjoint of the full 2^22-pair batch in the bench's launch configuration (autotuned
+    forward and adjoint tables); the per-read gradients of 40 sampled regions (every pair of
+    those reads, 2,560 pairs) are compared with the oracle's adjoint of those regions."""
+    import torch
+    b = synth.c4_persistent()
+    db = phmm.DeviceBatch(b)
+    o = phmm.autotune(db, which=3)
+    plan = phmm.Plan(db, o)
+    plan.forward()
+    P = len(b["pair_read"])
+    dy = np.random.default_rng(12).uniform(-1, 1, P)
+    gb, gi, gd, gg = plan.backward(torch.as_tensor(dy, device="cuda"))
+    gb, gi, gd = gb.cpu().numpy(), gi.cpu().numpy(), gd.cpu().numpy()
+    # regions hold reads 16 r .. 16 r + 15; every pair of a sampled read is taken
+    regions = np.random.default_rng(13).choice(65536, 40, replace=False)
+    reads = np.sort(np.concatenate([np.arange(16 * r, 16 * r + 16) for r in regions]))
+    pairs = np.nonzero(np.isin(b["pair_read"], reads))[0]
+    assert len(pairs) == 40 * 64
+    sb = synth.subset_pairs(b, pairs)
+    # the oracle over the sampled pairs only: the sampled reads' gradients are complete there
+    wy, wb, wi, wd, wg = oracle.backward_batch(sb, dy[pairs])
+    ro = b["read_off"]
+    idx = np.concatenate([np.arange(ro[r], ro[r + 1]) for r in reads])
+    grad_close(gb[idx], wb[idx], "d/dbq")
+    grad_close(gi[idx], wi[idx], "d/diq")
+    grad_close(gd[idx], wd[idx], "d/ddq")

@@ -205,10 +205,15 @@ def test_invalid_inputs_are_rejected(phmm):
 
 
 def test_c4_sampled_pairs_full_size_launch(phmm):
-    """C4 at full size (2^22 pairs) in the bench's launch configuration; a stratified sample
-    of pairs (every length bin, the longest ones) is compared with the oracle."""
+    """C4 at full size (2^22 pairs) in the bench's launch configuration (autotuned group
+    tables); a stratified sample of pairs (every length bin, the longest ones) is compared
+    with the oracle."""
     b = synth.c4_persistent()
-    got, flags, plan = run(phmm, b)
+    db = phmm.DeviceBatch(b)
+    o = phmm.autotune(db, which=1)
+    plan = phmm.Plan(db, o)
+    out, fl = plan.forward()
+    got, flags = out.cpu().numpy(), fl.cpu().numpy()
     assert np.all((flags & phmm.FLAG_INVALID) == 0)
     rl = np.diff(b["read_off"])[b["pair_read"]]
     hl = np.diff(b["hap_off"])[b["pair_hap"]]
