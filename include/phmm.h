@@ -99,7 +99,7 @@ typedef struct phmm_options {
   int32_t rows;        /* fixed group when binning == 0: rows per lane, 4/8/12/16/20 */
   int32_t persistent;  /* 1: persistent work-queue kernels; 0: one warp group per item */
   int32_t use_graph;   /* 1: replay the launch sequence from a captured CUDA graph */
-  int32_t warps_per_block; /* 0 = automatic */
+  int32_t warps_per_block; /* 1..4 warps per block (0 = 4) */
   int32_t bin_rows[PHMM_MAX_READ_LEN / 4 + 1]; /* optional read-length -> group table */
   int32_t bin_table_valid; /* 1 if bin_rows holds a table */
   int32_t adjoint_rescue;  /* 1: adjoints out of the FP32 range are redone in FP64; 0: NaN */
@@ -197,7 +197,9 @@ int phmm_plan_rescue_counts(phmm_plan *plan, const void *ws, void *stream, int64
  * events around phmm_forward (which & 1) and phmm_backward (which & 2).  The fastest group
  * of each range is written into opt->bin_rows / opt->bwd_rows (other entries: -1, meaning
  * the built-in default, or the caller's previous entries) and bin_table_valid /
- * bwd_table_valid are set.  The other fields of *opt are used as given.
+ * bwd_table_valid are set.  Then warps_per_block (1, 2 or 4: pairs per block = warps x the
+ * group's pairs per warp) is timed with the tuned tables on a strided sample of the whole
+ * batch and the fastest is written.  The other fields of *opt are used as given.
  *
  * The batch is validated as by phmm_plan_create (same errors).  Allocates temporary device
  * memory with cudaMallocAsync on `stream`, copies the offsets and pair lists to the host

@@ -92,6 +92,13 @@ static size_t bwd_smem(int K, int elem, int block) {
   return (size_t)(block / 32) * bwd_warp_bytes(K, elem);
 }
 
+// Threads per block of an adjoint launch: warps_per_block warps, fewer where their shared
+// memory would exceed the per-block limit.
+static int bwd_block(int K, int elem, int warps_per_block) {
+  const int fit = (int)((size_t)227 * 1024 / bwd_warp_bytes(K, elem));
+  return 32 * std::max(1, std::min(warps_per_block, fit));
+}
+
 // Read length -> FP32 backward group (rows per lane <= 12 keeps the adjoint in registers).
 int bwd_default_cfg(int m) {
   struct Gp { int cap, L, K; };
@@ -129,7 +136,7 @@ struct BwdLayout {
 
 static BwdLayout bwd_layout(const phmm_plan *pl) {
   const phmm_batch &b = plan_batch(pl);
-  const int block = 32 * plan_options(pl).warps_per_block;
+  const int wpb = plan_options(pl).warps_per_block;
   BwdLayout Lo;
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -145,6 +152,7 @@ static BwdLayout bwd_layout(const phmm_plan *pl) {
   const int64_t nmax = plan_n_max(pl);
   for (int cfg : plan_bwd_used(pl)) {
     const int L = cfg_lanes(cfg), K = cfg_rows(cfg);
+    const int block = bwd_block(K, 4, wpb);
     const size_t nslot = (size_t)plan_sms(pl) *
                          blocks_per_sm(bwd_kernel32(L, K), bwd_smem(K, 4, block), block) *
                          (block / 32);
@@ -152,6 +160,7 @@ static BwdLayout bwd_layout(const phmm_plan *pl) {
   }
   for (int c = 0; c < kNumCfg64; ++c) {
     const int K = rows64(c);
+    const int block = bwd_block(K, 8, wpb);
     const size_t nslot = (size_t)plan_sms(pl) *
                          blocks_per_sm(bwd_kernel64(K), bwd_smem(K, 8, block), block) *
                          (block / 32);
@@ -239,7 +248,6 @@ int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, floa
     a.resc_count = rcnt;
     a.why = (int32_t *)(ws + plan_layout_bin(pl, 10));
     CKB(cudaMemsetAsync(a.why, 0, 16, s));
-    const int block = 32 * o.warps_per_block;
     const int64_t nmax = plan_n_max(pl);
     CKB(cudaEventRecord(ev3[0], s));
     for (int cfg : plan_bwd_used(pl)) {
@@ -254,6 +262,7 @@ int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, floa
       c.rescue = o.adjoint_rescue ? 0 : 1;  // without the FP64 pass, failures write NaN
       BwdKernel k = bwd_kernel32(L, K);
       if (!k) return (int)cudaErrorInvalidValue;
+      const int block = bwd_block(K, 4, o.warps_per_block);
       const size_t sm = bwd_smem(K, 4, block);
       const int grid = plan_sms(pl) * blocks_per_sm(k, sm, block);
       k<<<grid, block, sm, s>>>(c);
@@ -272,6 +281,7 @@ int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, floa
       c.slot_elems = slot_elems(32, K, 8, nmax);
       c.rescue = 1;
       BwdKernel kk = bwd_kernel64(K);
+      const int block = bwd_block(K, 8, o.warps_per_block);
       const size_t sm = bwd_smem(K, 8, block);
       const int grid = plan_sms(pl) * blocks_per_sm(kk, sm, block);
       kk<<<grid, block, sm, s>>>(c);

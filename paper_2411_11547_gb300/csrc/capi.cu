@@ -265,7 +265,7 @@ int phmm_plan_create(const phmm_batch *batch, const phmm_options *opt, void *str
   if (!o.binning && !valid_group(o.lanes, o.rows)) return PHMM_EINVAL;
   (void)cudaGetLastError();  // drop a stale error left by an unrelated call
   if (o.warps_per_block <= 0) o.warps_per_block = 4;
-  if (o.warps_per_block > 8) return PHMM_EINVAL;
+  if (o.warps_per_block > 4) return PHMM_EINVAL;  // the kernels are built for <= 128 threads
   cudaStream_t s = (cudaStream_t)stream;
 
   // offsets to the host: monotone from 0, non-empty sequences, read length bound

@@ -283,6 +283,37 @@ extern "C" int phmm_autotune(const phmm_batch *batch, phmm_options *opt, int whi
       for (int bk = 4 * k + 1; bk <= 4 * k + 4; ++bk) tab[bk] = best;
     }
   }
+  // Warps per block (pairs per block = warps x pairs per warp; the kernels take up to 4
+  // warps per block) for the tuned tables: timed
+  // on a strided sample of the whole batch, forward and adjoint as requested.
+  {
+    std::vector<int64_t> sel;
+    const int64_t want = std::min<int64_t>(b.n_pairs, 4 * sample_pairs);
+    const int64_t stride = std::max<int64_t>(1, b.n_pairs / want);
+    for (int64_t p = 0; p < b.n_pairs && (int64_t)sel.size() < want; p += stride)
+      if (ro[pr[p] + 1] - ro[pr[p]] <= PHMM_MAX_READ_LEN) sel.push_back(p);
+    if (!sel.empty()) {
+      SubBatch sb;
+      if (make_sub(b, ro, ho, pr, ph, sel, s, sb) != cudaSuccess) return PHMM_ECUDA;
+      int best = work.warps_per_block;
+      float best_ms = 0.f;
+      for (int wpb : {1, 2, 4}) {
+        phmm_options o = work;
+        o.warps_per_block = wpb;
+        float ms = 0.f;
+        for (int pass = 1; pass <= 2; ++pass) {
+          if (!(which & pass)) continue;
+          const float t = time_candidate(sb, o, pass, s);
+          ms = (t < 0.f || ms < 0.f) ? -1.f : ms + t;
+        }
+        if (ms > 0.f && (best_ms == 0.f || ms < best_ms)) {
+          best = wpb;
+          best_ms = ms;
+        }
+      }
+      work.warps_per_block = best;
+    }
+  }
   *opt = work;
   return PHMM_OK;
 }
