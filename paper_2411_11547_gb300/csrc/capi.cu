@@ -7,6 +7,7 @@
 #include <mutex>
 #include <new>
 #include <vector>
+#include <nvtx3/nvToolsExt.h>
 #include "fwd_inst.cuh"
 #include "phmm_internal.cuh"
 
@@ -207,6 +208,11 @@ static void make_layout(phmm_plan *pl) {
   L.total = o;
 }
 
+namespace phmm {
+NvtxRange::NvtxRange(const char *name) { nvtxRangePushA(name); }
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
+}  // namespace phmm
+
 extern "C" {
 
 void phmm_options_default(phmm_options *opt) {
@@ -244,6 +250,7 @@ static bool valid_group(int L, int K) {
 
 int phmm_plan_create(const phmm_batch *batch, const phmm_options *opt, void *stream,
                      phmm_plan **out) {
+  const phmm::NvtxRange nvtx("phmm_plan_create");
   if (!batch || !out) return PHMM_EINVAL;
   *out = nullptr;
   const phmm_batch &b = *batch;
@@ -504,6 +511,7 @@ extern "C" {
 
 int phmm_forward(phmm_plan *pl, void *ws, size_t ws_bytes, double *out, uint8_t *flags,
                  void *stream) {
+  const phmm::NvtxRange nvtx("phmm_forward");
   if (!pl || !ws || (pl->b.n_pairs > 0 && (!out || !flags))) return PHMM_EINVAL;
   if (((uintptr_t)ws & 255) != 0) return PHMM_EINVAL;
   if (ws_bytes < pl->L.total) return PHMM_ENOMEM;
@@ -545,6 +553,7 @@ int phmm_forward(phmm_plan *pl, void *ws, size_t ws_bytes, double *out, uint8_t 
 
 int phmm_backward(phmm_plan *pl, void *ws, size_t ws_bytes, const double *dL, float *dbq,
                   float *diq, float *ddq, double *dgcp, void *stream) {
+  const phmm::NvtxRange nvtx("phmm_backward");
   if (!pl || !ws || !dgcp) return PHMM_EINVAL;
   if (pl->sum_m > 0 && (!dbq || !diq || !ddq)) return PHMM_EINVAL;
   if (pl->b.n_pairs > 0 && !dL) return PHMM_EINVAL;

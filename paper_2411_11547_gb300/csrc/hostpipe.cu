@@ -17,6 +17,7 @@
 #include <thread>
 #include <vector>
 #include "phmm.h"
+#include "phmm_internal.cuh"
 
 namespace {
 
@@ -133,6 +134,7 @@ extern "C" void phmm_score_host_release(void) {
 
 extern "C" int phmm_score_host(const phmm_batch *hb, const phmm_options *opt,
                                int64_t subset_cells, double *out_log10, uint8_t *out_flags) {
+  const phmm::NvtxRange nvtx("phmm_score_host");
   if (!hb || !out_log10 || !out_flags || subset_cells < 1) return PHMM_EINVAL;
   const phmm_batch &b = *hb;
   if (b.n_reads < 1 || b.n_haps < 1 || b.n_pairs < 0) return PHMM_EINVAL;

@@ -76,6 +76,15 @@ struct FwdArgs {
   int64_t tile_cols;        // columns per tile buffer (the longest haplotype)
 };
 
+// Host-side NVTX range over a library call (profilers show the calls on their timelines;
+// the markers cost nothing without a tool attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name);
+  ~NvtxRange();
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 // Launchers (one per precision); return cudaError_t of the launch.
 int launch_fwd32(int cfg, bool ext, int grid, int block, cudaStream_t s, const FwdArgs &a);
 int launch_fwd64(int cfg64, bool ext, int grid, int block, cudaStream_t s, const FwdArgs &a);

@@ -217,6 +217,7 @@ static float time_candidate(const SubBatch &sb, const phmm_options &opt, int whi
 
 extern "C" int phmm_autotune(const phmm_batch *batch, phmm_options *opt, int which,
                              int64_t sample_pairs, void *stream) {
+  const phmm::NvtxRange nvtx("phmm_autotune");
   if (!batch || !opt || which < 1 || which > 3 || sample_pairs < 1) return PHMM_EINVAL;
   cudaGetLastError();
   cudaStream_t s = (cudaStream_t)stream;

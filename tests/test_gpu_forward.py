@@ -260,3 +260,18 @@ def test_long_reads_in_row_tiles(phmm, first_line):
     with pytest.raises(phmm.PhmmError) as e:
         plan.backward(torch.ones(len(got), dtype=torch.float64, device="cuda"))
     assert e.value.status == phmm.PHMM_ETOOLONG
+
+
+def test_metamorphic_order_blocks_and_bins(phmm):
+    """The result of a pair does not depend on the batch order, on pairs per block (warps per
+    block) or on bin edges that keep its group: bitwise.  Across groups: within tolerance."""
+    b = synth.c1_batched(regions=5)
+    base, bflags, _ = run(phmm, b)
+    perm = np.random.default_rng(8).permutation(len(b["pair_read"]))
+    pb = dict(b, pair_read=b["pair_read"][perm].copy(), pair_hap=b["pair_hap"][perm].copy())
+    for wpb in (1, 2, 4):
+        got, flags, _ = run(phmm, pb, warps_per_block=wpb)
+        assert np.array_equal(got, base[perm]) and np.array_equal(flags, bflags[perm])
+    # bin edges moved: reads of every length scored by the wider 32 x 16 group
+    got, flags, _ = run(phmm, b, bin_rows=[3 * 9 + 6] * 129)
+    assert np.max(np.abs(got - base)) <= 2e-4
