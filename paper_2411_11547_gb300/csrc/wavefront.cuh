@@ -27,6 +27,7 @@
 //          to rounding because the recurrences are linear; never underflows.
 #pragma once
 #include <cmath>
+#include <type_traits>
 #include "phmm_internal.cuh"
 
 namespace phmm {
@@ -266,6 +267,150 @@ __device__ __forceinline__ void wf_rescale(WfState<T, K> &st, int t) {
   st.f = Num<T>::exp2i(t == 0 ? -st.E : Eup - st.E - kBias * (K - 1));
 }
 
+// ---- packed FP32 path (fma.rn.f32x2 / mul.rn.f32x2: two lane operations per instruction,
+// each rounded exactly as its scalar counterpart) --------------------------------------------
+__device__ __forceinline__ unsigned long long pk2(float2 v) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1,%2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+  return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long r) {
+  float2 v;
+  asm("mov.b64 {%0,%1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+  return v;
+}
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
+  return upk2(d);
+}
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(d);
+}
+
+// Lane state of the packed path: pair p holds rows p and p + K/2, so the row above a pair
+// (rows p-1, p-1+K/2) is again one pair (for p = 0: the strip's input row and row K/2-1).
+template <int K>
+struct WfState2 {
+  static constexpr int H = K / 2;
+  float2 M[H], I[H], D[H];  // D holds D/zeta (Eq. 3 over zeta, as the PRIMED scalar step)
+  float Md, Sd, acc, f;
+  int E, c;
+};
+
+// The emission table of the packed path stores a lane's rows interleaved (p, p + K/2, p+1,
+// ...): table position -> row.
+template <int K>
+__host__ __device__ constexpr int x2_row(int pos) {
+  return (pos & 1) ? K / 2 + pos / 2 : pos / 2;
+}
+
+// One wavefront step of the packed path (extended-range FP32, D/zeta form; the same
+// arithmetic as wf_step<float, L, K, true, true> per lane operation): 3.5 instructions per
+// cell instead of 6; only the I chain down the rows (Eq. 2) stays scalar.
+template <int L, int K, bool TOP = false>
+__device__ __forceinline__ void wf_step_x2(WfState2<K> &st, int cu, int t, float bnd, float eps,
+                                           const float *tbl, const float2 (&ap)[K / 2],
+                                           const float2 (&dl)[K / 2], const float2 (&zt)[K / 2],
+                                           const float2 (&ei)[K / 2], float tM = 0.f,
+                                           float tI = 0.f, float tT = 0.f) {
+  constexpr unsigned FULL = 0xffffffffu;
+  constexpr int H = K / 2;
+  constexpr int CS = TableGeom<float, K>::CS;
+  const int cin = __shfl_up_sync(FULL, st.c, 1, L);
+  st.c = (t == 0) ? cu : cin;
+  const float third = fmaf(zt[H - 1].y, st.D[H - 1].y, st.I[H - 1].y);  // I + D of row K-1
+  float inM = __shfl_up_sync(FULL, st.M[H - 1].y, 1, L);
+  float inI = __shfl_up_sync(FULL, st.I[H - 1].y, 1, L);
+  float inD = __shfl_up_sync(FULL, third, 1, L);
+  if (t == 0) {
+    if constexpr (TOP) {
+      inM = tM;
+      inI = tI;
+      inD = tT;
+    } else {
+      inM = 0.f;
+      inI = bnd;
+      inD = bnd;
+    }
+  }
+  const float fe = (TOP && t == 0) ? 1.f : st.f;
+  inM *= fe;
+  inI *= fe;
+  inD *= fe;
+  float e[K];
+  load_rows<float, K>(tbl + st.c * CS, e);
+  // I + D (= I + zeta D') of every row at the previous column, before the update
+  float2 S[H];
+#pragma unroll
+  for (int p = 0; p < H; ++p) S[p] = ffma2(zt[p], st.D[p], st.I[p]);
+  const float Mtop = st.M[H - 1].x, Stop = S[H - 1].x;  // row K/2-1, previous column
+  const float2 eps2 = make_float2(eps, eps);
+#pragma unroll
+  for (int p = H - 1; p >= 0; --p) {
+    const float2 md = p ? st.M[p - 1] : make_float2(st.Md, Mtop);
+    const float2 sd = p ? S[p - 1] : make_float2(st.Sd, Stop);
+    st.D[p] = ffma2(eps2, st.D[p], st.M[p]);                               // Eq. 3 over zeta
+    st.M[p] = fmul2(make_float2(e[2 * p], e[2 * p + 1]), ffma2(ap[p], md, sd));  // Eq. 1
+  }
+  // Eq. 2 down the rows: the products with the new M of the row above in pairs, the chain
+  // through I scalar (rows 0 .. K/2-1, then K/2 .. K-1)
+  float2 dM[H];
+#pragma unroll
+  for (int p = 0; p < H; ++p)
+    dM[p] = fmul2(dl[p], p ? st.M[p - 1] : make_float2(inM, st.M[H - 1].x));
+  float prev = inI;
+#pragma unroll
+  for (int p = 0; p < H; ++p) {
+    st.I[p].x = fmaf(ei[p].x, prev, dM[p].x);
+    prev = st.I[p].x;
+  }
+#pragma unroll
+  for (int p = 0; p < H; ++p) {
+    st.I[p].y = fmaf(ei[p].y, prev, dM[p].y);
+    prev = st.I[p].y;
+  }
+  st.Md = inM;
+  st.Sd = inD;
+  st.acc += st.M[H - 1].y + st.I[H - 1].y;
+}
+
+// Per-lane renormalisation of the packed state (as wf_rescale).
+template <int L, int K, int kBias>
+__device__ __forceinline__ void wf_rescale_x2(WfState2<K> &st, int t) {
+  constexpr unsigned FULL = 0xffffffffu;
+  constexpr int H = K / 2;
+  float mx = fmaxf(st.Md, st.Sd);
+#pragma unroll
+  for (int p = 0; p < H; ++p)
+    mx = fmaxf(mx, fmaxf(fmaxf(fmaxf(st.M[p].x, st.M[p].y), fmaxf(st.I[p].x, st.I[p].y)),
+                         fmaxf(st.D[p].x, st.D[p].y)));
+  if (t == L - 1) mx = fmaxf(mx, st.acc);
+  const bool zero = !(mx > 0.f);
+  if (!zero) {
+    const int En = st.E + Num<float>::ilog2(mx);
+    const float sc = Num<float>::exp2i(st.E - En);
+    const float2 sc2 = make_float2(sc, sc);
+#pragma unroll
+    for (int p = 0; p < H; ++p) {
+      st.M[p] = fmul2(st.M[p], sc2);
+      st.I[p] = fmul2(st.I[p], sc2);
+      st.D[p] = fmul2(st.D[p], sc2);
+    }
+    st.Md *= sc;
+    st.Sd *= sc;
+    st.acc *= sc;
+    st.E = En;
+  }
+  const float xb = fmaxf(st.M[H - 1].y, fmaxf(st.I[H - 1].y, st.D[H - 1].y));
+  const int Eup = __shfl_up_sync(FULL, st.E, 1, L);
+  const float xbu = __shfl_up_sync(FULL, xb, 1, L);
+  if (zero && t > 0) st.E = Eup - kBias * (K - 1) + (xbu > 0.f ? Num<float>::ilog2(xbu) : 0);
+  st.f = Num<float>::exp2i(t == 0 ? -st.E : Eup - st.E - kBias * (K - 1));
+}
+
 // Minimum resident blocks per SM the compiler must allow (register budget): rows per lane set
 // how many per-row registers a lane holds.
 template <typename T, int K>
@@ -279,6 +424,9 @@ __global__ void __launch_bounds__(128, wf_min_blocks<T, K>()) wf_forward(const F
   constexpr int G = 32 / L;
   constexpr int VW = G_::VW, LS = G_::LS, CS = G_::CS;
   constexpr unsigned FULL = 0xffffffffu;
+  // packed FP32 pairs of rows for the extended-range FP32 tier
+  constexpr bool X2 = EXT && sizeof(T) == 4;
+  constexpr int H = K / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int t = lane % L, sub = lane / L;
@@ -365,12 +513,12 @@ __global__ void __launch_bounds__(128, wf_min_blocks<T, K>()) wf_forward(const F
       T ev[kCodes][VW];
 #pragma unroll
       for (int u = 0; u < VW; ++u) {
-        const int rr = r0v + u;
-        if (rr >= K) {  // table padding past the lane's rows
+        if (r0v + u >= K) {  // table padding past the lane's rows
 #pragma unroll
           for (int c = 0; c < kCodes; ++c) ev[c][u] = 0;
           continue;
         }
+        const int rr = X2 ? x2_row<K>(r0v + u) : r0v + u;  // the row at this table position
         // 0-based read position; < 0: pad row
         const int pos = tile * LK + t * K + rr - npad;
         const T bias = rr ? (T)(1 << kBias) : (T)1;
@@ -405,18 +553,32 @@ __global__ void __launch_bounds__(128, wf_min_blocks<T, K>()) wf_forward(const F
     // ---- wavefront ------------------------------------------------------------------------
     int steps = n > 0 ? (int)n + L - 1 : 0;
     steps = __reduce_max_sync(FULL, steps);
-    WfState<T, K> st;
+    typename std::conditional<X2, WfState2<K>, WfState<T, K>>::type st;
     st.c = kNull;
     st.Md = 0;
     st.Sd = (t == 0 && tile == 0) ? bnd : (T)0;
     st.acc = 0;
     st.f = t == 0 ? (T)1 : Num<T>::exp2i(-kBias * (K - 1));
     st.E = 0;
+    float2 ap2[X2 ? H : 1], dl2[X2 ? H : 1], zt2[X2 ? H : 1], ei2[X2 ? H : 1];
+    if constexpr (X2) {
 #pragma unroll
-    for (int r = 0; r < K; ++r) {
-      st.M[r] = M[r];
-      st.I[r] = I[r];
-      st.D[r] = D[r];
+      for (int q = 0; q < H; ++q) {
+        st.M[q] = make_float2(M[q], M[q + H]);
+        st.I[q] = make_float2(I[q], I[q + H]);
+        st.D[q] = make_float2(D[q], D[q + H]);
+        ap2[q] = make_float2(ap[q], ap[q + H]);
+        dl2[q] = make_float2(dl[q], dl[q + H]);
+        zt2[q] = make_float2(zt[q], zt[q + H]);
+        ei2[q] = make_float2(ei[q], ei[q + H]);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < K; ++r) {
+        st.M[r] = M[r];
+        st.I[r] = I[r];
+        st.D[r] = D[r];
+      }
     }
     if constexpr (TILED && EXT) {
       // lane 0 of a lower tile starts at the exponent that brings column 1 of the row above
@@ -456,19 +618,31 @@ __global__ void __launch_bounds__(128, wf_min_blocks<T, K>()) wf_forward(const F
           tI = bI * cv;
           tT = bX * cv;
         }
-        wf_step<T, L, K, EXT, EXT, false, true>(st, code, t, bnd, eps, tbl, ap, dl, zt, ei,
-                                                in3, tM, tI, tT);
+        if constexpr (X2) {
+          wf_step_x2<L, K, true>(st, code, t, bnd, eps, tbl, ap2, dl2, zt2, ei2, tM, tI, tT);
+        } else {
+          wf_step<T, L, K, EXT, EXT, false, true>(st, code, t, bnd, eps, tbl, ap, dl, zt, ei,
+                                                  in3, tM, tI, tT);
+        }
         if (!last_tile && t == L - 1) {
           const int64_t j = (int64_t)s + 1 - (L - 1);  // the last lane's column
           if (j >= 1 && j <= n) {
             TileCol<T> o;
-            o.M = st.M[K - 1];
-            o.I = st.I[K - 1];
-            o.X = EXT ? st.I[K - 1] + zt[K - 1] * st.D[K - 1] : st.D[K - 1];
+            if constexpr (X2) {
+              o.M = st.M[H - 1].y;
+              o.I = st.I[H - 1].y;
+              o.X = fmaf(zt2[H - 1].y, st.D[H - 1].y, st.I[H - 1].y);
+            } else {
+              o.M = st.M[K - 1];
+              o.I = st.I[K - 1];
+              o.X = EXT ? st.I[K - 1] + zt[K - 1] * st.D[K - 1] : st.D[K - 1];
+            }
             o.E = (T)st.E;
             tb_out[j - 1] = o;
           }
         }
+      } else if constexpr (X2) {
+        wf_step_x2<L, K>(st, code, t, bnd, eps, tbl, ap2, dl2, zt2, ei2);
       } else {
         wf_step<T, L, K, EXT, EXT>(st, code, t, bnd, eps, tbl, ap, dl, zt, ei, in3);
       }
@@ -494,7 +668,8 @@ __global__ void __launch_bounds__(128, wf_min_blocks<T, K>()) wf_forward(const F
         Efin = st.E;
         done = true;
       }
-      if constexpr (EXT) wf_rescale<T, L, K, kBias>(st, t);
+      if constexpr (X2) wf_rescale_x2<L, K, kBias>(st, t);
+      else if constexpr (EXT) wf_rescale<T, L, K, kBias>(st, t);
     }
     for (int s0 = ramp; s0 < steps; s0 += 16) {
       hv = (t == 0 && s0 < n) ? *reinterpret_cast<const uint4 *>(a.hcode + hs + s0) : null16;
@@ -509,7 +684,8 @@ __global__ void __launch_bounds__(128, wf_min_blocks<T, K>()) wf_forward(const F
         Efin = st.E;
         done = true;
       }
-      if constexpr (EXT) wf_rescale<T, L, K, kBias>(st, t);
+      if constexpr (X2) wf_rescale_x2<L, K, kBias>(st, t);
+      else if constexpr (EXT) wf_rescale<T, L, K, kBias>(st, t);
     }
     if (!done) {
       Sfin = st.acc;
