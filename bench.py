@@ -441,7 +441,8 @@ def main():
                    "group_tables": ("built-in" if args.no_tune else
                                     f"phmm_autotune (32768-pair samples per 16-row read-length "
                                     f"range, {t_tune:.2f} s, outside the timed region)"),
-                   "warps_per_block": int(opts.warps_per_block)},
+                   "warps_per_block": {"forward": int(opts.warps_per_block),
+                                       "adjoint": int(opts.bwd_warps_per_block)}},
         "fwd_gcups": fwd_gcups,
         "fwd_wavefront_gcups": cells / (wf * 1e-3) / 1e9,
         "fwd_rescue_ms": statistics.median(resc_ms),

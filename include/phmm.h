@@ -105,6 +105,7 @@ typedef struct phmm_options {
   int32_t adjoint_rescue;  /* 1: adjoints out of the FP32 range are redone in FP64; 0: NaN */
   int32_t bwd_rows[PHMM_MAX_READ_LEN / 4 + 1]; /* optional read-length -> adjoint group table */
   int32_t bwd_table_valid; /* 1 if bwd_rows holds a table */
+  int32_t bwd_warps_per_block; /* adjoint launches: 1..4 (0 = warps_per_block) */
 } phmm_options;
 
 void phmm_options_default(phmm_options *opt);
@@ -194,12 +195,13 @@ int phmm_plan_rescue_counts(phmm_plan *plan, const void *ws, void *stream, int64
  * read-length range that holds pairs, a strided sample of at most `sample_pairs` of its
  * pairs is gathered into a compact device batch and each built group (lanes x rows) whose
  * capacity covers the range, up to twice the range's longest read, is timed with CUDA
- * events around phmm_forward (which & 1) and phmm_backward (which & 2).  The fastest group
- * of each range is written into opt->bin_rows / opt->bwd_rows (other entries: -1, meaning
- * the built-in default, or the caller's previous entries) and bin_table_valid /
- * bwd_table_valid are set.  Then warps_per_block (1, 2 or 4: pairs per block = warps x the
- * group's pairs per warp) is timed with the tuned tables on a strided sample of the whole
- * batch and the fastest is written.  The other fields of *opt are used as given.
+ * events around phmm_forward (which & 1, on samples 8x larger) and phmm_backward (which & 2).
+ * The fastest group of each range is written into opt->bin_rows / opt->bwd_rows if it beats
+ * the built-in group by at least 2% (other entries: -1, meaning the built-in default, or the
+ * caller's previous entries) and bin_table_valid / bwd_table_valid are set.  Then warps_per_block (forward) and bwd_warps_per_block (adjoint),
+ * each 1, 2 or 4 (pairs per block = warps x the group's pairs per warp), are timed with the
+ * tuned tables on a strided sample of the whole batch and the fastest are written.  The other
+ * fields of *opt are used as given.
  *
  * The batch is validated as by phmm_plan_create (same errors).  Allocates temporary device
  * memory with cudaMallocAsync on `stream`, copies the offsets and pair lists to the host

@@ -136,7 +136,7 @@ struct BwdLayout {
 
 static BwdLayout bwd_layout(const phmm_plan *pl) {
   const phmm_batch &b = plan_batch(pl);
-  const int wpb = plan_options(pl).warps_per_block;
+  const int wpb = plan_options(pl).bwd_warps_per_block;
   BwdLayout Lo;
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -262,7 +262,7 @@ int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, floa
       c.rescue = o.adjoint_rescue ? 0 : 1;  // without the FP64 pass, failures write NaN
       BwdKernel k = bwd_kernel32(L, K);
       if (!k) return (int)cudaErrorInvalidValue;
-      const int block = bwd_block(K, 4, o.warps_per_block);
+      const int block = bwd_block(K, 4, o.bwd_warps_per_block);
       const size_t sm = bwd_smem(K, 4, block);
       const int grid = plan_sms(pl) * blocks_per_sm(k, sm, block);
       k<<<grid, block, sm, s>>>(c);
@@ -281,7 +281,7 @@ int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, floa
       c.slot_elems = slot_elems(32, K, 8, nmax);
       c.rescue = 1;
       BwdKernel kk = bwd_kernel64(K);
-      const int block = bwd_block(K, 8, o.warps_per_block);
+      const int block = bwd_block(K, 8, o.bwd_warps_per_block);
       const size_t sm = bwd_smem(K, 8, block);
       const int grid = plan_sms(pl) * blocks_per_sm(kk, sm, block);
       kk<<<grid, block, sm, s>>>(c);

@@ -691,8 +691,8 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
 using BwdKernel = void (*)(const BwdArgs);
 
 // Instantiation tables (nullptr where a group is not built).  FP32: lanes 4..32, rows per
-// lane 4/6/8/10/12 (and 16 with 32 lanes, for reads up to 512); FP64 hand-off groups: 32
-// lanes x rows 4/8/16.
+// lane 4/6/8/10/12 (also 14 with 16 lanes, and 16 with 32 lanes for reads up to 512); FP64
+// hand-off groups: 32 lanes x rows 4/8/16.
 BwdKernel bwd32_lo(int L, int K);   // L in {4, 8}
 BwdKernel bwd32_mid(int L, int K);  // L = 16
 BwdKernel bwd32_hi(int L, int K);   // L = 32

@@ -104,7 +104,7 @@ int launch_fwd64(int cfg64, bool ext, int grid, int block, cudaStream_t s, const
 
 // Default read-length -> group table: the lanes x rows group with the fewest pad rows,
 // fewer lanes on a tie (shorter wavefront ramp, more rows to amortise each step's exchange).
-static int default_cfg_of_m(int m) {
+int default_cfg_of_m(int m) {
   int best = -1, best_cap = 1 << 30;
   for (int L = 4; L <= 32; L *= 2) {
     int K = (m + L - 1) / L;
@@ -273,6 +273,8 @@ int phmm_plan_create(const phmm_batch *batch, const phmm_options *opt, void *str
   (void)cudaGetLastError();  // drop a stale error left by an unrelated call
   if (o.warps_per_block <= 0) o.warps_per_block = 4;
   if (o.warps_per_block > 4) return PHMM_EINVAL;  // the kernels are built for <= 128 threads
+  if (o.bwd_warps_per_block <= 0) o.bwd_warps_per_block = o.warps_per_block;
+  if (o.bwd_warps_per_block > 4) return PHMM_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
 
   // offsets to the host: monotone from 0, non-empty sequences, read length bound

@@ -17,6 +17,8 @@
 
 namespace phmm {
 int bwd_cfg_supported(int cfg);
+int bwd_default_cfg(int m);
+int default_cfg_of_m(int m);
 }
 
 namespace {
@@ -245,20 +247,26 @@ extern "C" int phmm_autotune(const phmm_batch *batch, phmm_options *opt, int whi
     if (m <= PHMM_MAX_READ_LEN) members[(m - 1) / kRange].push_back(p);  // longer: row tiles
   }
   phmm_options work = *opt;  // ranges without pairs keep the caller's entries
+  // A tuned choice replaces the built-in one only if it is at least this much faster: timings
+  // of samples carry noise and some bias against the whole batch.
+  constexpr float kMargin = 0.98f;
   for (int k = 0; k < kRanges; ++k) {
     const std::vector<int64_t> &mem = members[k];
     if (mem.empty()) continue;
-    std::vector<int64_t> sel;
-    const int64_t stride = std::max<int64_t>(1, (int64_t)mem.size() / sample_pairs);
-    for (size_t i = 0; i < mem.size() && (int64_t)sel.size() < sample_pairs; i += stride)
-      sel.push_back(mem[i]);
-    SubBatch sb;
-    if (make_sub(b, ro, ho, pr, ph, sel, s, sb) != cudaSuccess) return PHMM_ECUDA;
     const int hi = kRange * (k + 1);
     for (int pass = 1; pass <= 2; ++pass) {
       if (!(which & pass)) continue;
+      // the forward is cheap: it is timed on samples 8x larger
+      const int64_t want = pass == 1 ? 8 * sample_pairs : sample_pairs;
+      std::vector<int64_t> sel;
+      const int64_t stride = std::max<int64_t>(1, (int64_t)mem.size() / want);
+      for (size_t i = 0; i < mem.size() && (int64_t)sel.size() < want; i += stride)
+        sel.push_back(mem[i]);
+      SubBatch sb;
+      if (make_sub(b, ro, ho, pr, ph, sel, s, sb) != cudaSuccess) return PHMM_ECUDA;
+      const int builtin = pass == 1 ? default_cfg_of_m(hi) : bwd_default_cfg(hi);
       int best = -1;
-      float best_ms = 0.f;
+      float best_ms = 0.f, builtin_ms = -1.f;
       for (int cfg = 0; cfg < kNumCfg32; ++cfg) {
         const int cap = cfg_lanes(cfg) * cfg_rows(cfg);
         if (cap < hi || cap > std::max(2 * hi, 64)) continue;
@@ -269,12 +277,15 @@ extern "C" int phmm_autotune(const phmm_batch *batch, phmm_options *opt, int whi
         for (int i = 0; i <= PHMM_MAX_READ_LEN / 4; ++i) tab[i] = cfg;
         if (pass == 1) o.bin_table_valid = 1; else o.bwd_table_valid = 1;
         const float ms = time_candidate(sb, o, pass, s);
+        if (cfg == builtin) builtin_ms = ms;
         if (ms > 0.f && (best < 0 || ms < best_ms)) {
           best = cfg;
           best_ms = ms;
         }
       }
-      if (best < 0) continue;  // no candidate ran: keep the default for this range
+      if (best < 0) continue;  // no candidate ran: keep the built-in entries
+      // not clearly faster than the built-in group: keep the built-in (per 4-row bucket) entries
+      if (builtin_ms > 0.f && best_ms > kMargin * builtin_ms) continue;
       int32_t *tab = pass == 1 ? work.bin_rows : work.bwd_rows;
       const int32_t *valid = pass == 1 ? &work.bin_table_valid : &work.bwd_table_valid;
       if (!*valid) {  // first tuned range: fill the table with "no entry" (default)
@@ -285,8 +296,8 @@ extern "C" int phmm_autotune(const phmm_batch *batch, phmm_options *opt, int whi
     }
   }
   // Warps per block (pairs per block = warps x pairs per warp; the kernels take up to 4
-  // warps per block) for the tuned tables: timed
-  // on a strided sample of the whole batch, forward and adjoint as requested.
+  // warps per block) for the tuned tables, forward and adjoint separately: timed on a strided
+  // sample of the whole batch.
   {
     std::vector<int64_t> sel;
     const int64_t want = std::min<int64_t>(b.n_pairs, 4 * sample_pairs);
@@ -296,23 +307,26 @@ extern "C" int phmm_autotune(const phmm_batch *batch, phmm_options *opt, int whi
     if (!sel.empty()) {
       SubBatch sb;
       if (make_sub(b, ro, ho, pr, ph, sel, s, sb) != cudaSuccess) return PHMM_ECUDA;
-      int best = work.warps_per_block;
-      float best_ms = 0.f;
-      for (int wpb : {1, 2, 4}) {
-        phmm_options o = work;
-        o.warps_per_block = wpb;
-        float ms = 0.f;
-        for (int pass = 1; pass <= 2; ++pass) {
-          if (!(which & pass)) continue;
-          const float t = time_candidate(sb, o, pass, s);
-          ms = (t < 0.f || ms < 0.f) ? -1.f : ms + t;
+      for (int pass = 1; pass <= 2; ++pass) {
+        if (!(which & pass)) continue;
+        int32_t &field = pass == 1 ? work.warps_per_block : work.bwd_warps_per_block;
+        const int current = field > 0 ? field : (pass == 2 && work.warps_per_block > 0
+                                                     ? work.warps_per_block : 4);
+        int best = current;
+        float best_ms = 0.f, current_ms = -1.f;
+        for (int wpb : {1, 2, 4}) {
+          phmm_options o = work;
+          (pass == 1 ? o.warps_per_block : o.bwd_warps_per_block) = wpb;
+          const float ms = time_candidate(sb, o, pass, s);
+          if (wpb == current) current_ms = ms;
+          if (ms > 0.f && (best_ms == 0.f || ms < best_ms)) {
+            best = wpb;
+            best_ms = ms;
+          }
         }
-        if (ms > 0.f && (best_ms == 0.f || ms < best_ms)) {
-          best = wpb;
-          best_ms = ms;
-        }
+        if (current_ms > 0.f && best_ms > kMargin * current_ms) best = current;
+        field = best;
       }
-      work.warps_per_block = best;
     }
   }
   *opt = work;

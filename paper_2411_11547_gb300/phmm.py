@@ -54,7 +54,7 @@ class Options(ctypes.Structure):
         ("bin_rows", ctypes.c_int32 * (PHMM_MAX_READ_LEN // 4 + 1)),
         ("bin_table_valid", ctypes.c_int32), ("adjoint_rescue", ctypes.c_int32),
         ("bwd_rows", ctypes.c_int32 * (PHMM_MAX_READ_LEN // 4 + 1)),
-        ("bwd_table_valid", ctypes.c_int32),
+        ("bwd_table_valid", ctypes.c_int32), ("bwd_warps_per_block", ctypes.c_int32),
     ]
 
 

@@ -30,9 +30,11 @@ def test_autotune_tables_and_parity(phmm):
     b = synth.random_pairs(123, 400, (1, 320), (1, 400), related=0.5, qual_dtype=np.float32)
     db = phmm.DeviceBatch(b)
     o = phmm.autotune(db, which=3, sample_pairs=48)
-    assert o.bin_table_valid == 1 and o.bwd_table_valid == 1
     m = np.diff(b["read_off"])
-    for tab, built in ((o.bin_rows, None), (o.bwd_rows, "bwd")):
+    for tab, built, valid in ((o.bin_rows, None, o.bin_table_valid),
+                              (o.bwd_rows, "bwd", o.bwd_table_valid)):
+        if not valid:  # no tuned group beat the built-in ones
+            continue
         tuned = 0
         for k in range(1, 129):
             c = tab[k]
@@ -41,11 +43,12 @@ def test_autotune_tables_and_parity(phmm):
             L, K = cfg_shape(c)
             assert L * K >= 4 * k, (k, c)
             if built == "bwd":
-                assert K in (4, 6, 8, 10, 12) or (L, K) == (32, 16)
+                assert K in (4, 6, 8, 10, 12) or (L, K) in ((16, 14), (32, 16))
             tuned += 1
-        # every 16-row range that holds pairs got an entry
+        # entries only in 16-row ranges that hold pairs (others keep the built-in groups)
         ranges = set(((m - 1) // 16).tolist())
-        assert tuned == 4 * len(ranges)
+        assert tuned <= 4 * len(ranges)
+        assert all(tab[k] < 0 for k in range(1, 129) if (4 * k - 1) // 16 not in ranges)
     plan = phmm.Plan(db, o)
     out, flags = plan.forward()
     want = oracle.forward_batch(b)

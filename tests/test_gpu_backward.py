@@ -154,7 +154,7 @@ def test_autograd_function(phmm):
     assert abs(float(gcp.grad) - wg) <= RTOL * abs(wg) + 1e-9
 
 
-BWD_SHAPES = [(L, K) for L in (4, 8, 16, 32) for K in (4, 6, 8, 10, 12)] + [(32, 16)]
+BWD_SHAPES = [(L, K) for L in (4, 8, 16, 32) for K in (4, 6, 8, 10, 12)] + [(16, 14), (32, 16)]
 
 
 @pytest.mark.parametrize("L,K", BWD_SHAPES)
