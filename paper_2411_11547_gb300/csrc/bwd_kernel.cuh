@@ -43,7 +43,7 @@ __host__ __device__ constexpr int rec_width(int K) { return rec_w(K, (int)sizeof
 // TableGeom) and the step records of one segment.  The segment length follows from what fits
 // next to the table at the occupancy the registers allow (warps per SM): 2 to 8 steps.
 __host__ __device__ constexpr int bwd_warps_per_sm(int K, int elem) {
-  return elem == 8 ? 4 : (K <= 4 ? 16 : (K <= 8 ? 12 : 8));
+  return elem == 8 ? 4 : (K <= 4 ? 16 : (K <= 6 ? 12 : 8));
 }
 __host__ __device__ constexpr size_t bwd_table_bytes(int K, int elem) {
   return (size_t)kCodes * 32 * elem *
@@ -182,7 +182,7 @@ __device__ __forceinline__ void adj_rescale(AdjState<T, K> &as, int t, T S, int 
 // state, adjoints, coefficients, five partial sums) grow with the rows per lane.
 template <typename T, int K>
 constexpr int bwd_min_blocks() {
-  return sizeof(T) == 8 ? 1 : (K <= 4 ? 4 : (K <= 8 ? 3 : 2));
+  return sizeof(T) == 8 ? 1 : (K <= 4 ? 4 : (K <= 6 ? 3 : 2));
 }
 
 template <typename T, int L, int K>
@@ -321,9 +321,30 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
     T Sfin = 0;
     int Efin = 0;
     bool done = false;
+    // Haplotype codes of segment qq's steps, 3 bits per step (the first lane of a pair reads
+    // them; the others take theirs from the lane above).  Loaded one segment ahead, so the
+    // load latency stays off the steps' dependency chain.
+    static_assert(3 * kSeg <= 31, "codes of a segment must fit one register");
+    auto seg_codes = [&](int qq) {
+      int cs = 0;
+      if (t == 0 && qq >= 0 && qq < nq) {
+        const int bb = qq < ramp ? qq : ramp + kSeg * (qq - ramp);
+        const int ll = qq < ramp ? 1 : kSeg;
+#pragma unroll
+        for (int u = 0; u < kSeg; ++u) {
+          const int s = bb + u;
+          const int c = (u < ll && s < n) ? (int)fa.hcode[hs + s] : kNull;
+          cs |= c << (3 * u);
+        }
+      }
+      return cs;
+    };
+    int segc = seg_codes(0);
     for (int q = 0; q < nq; ++q) {
       const int b = q < ramp ? q : ramp + kSeg * (q - ramp);
       const int len = q < ramp ? 1 : kSeg;
+      const int cur = segc;
+      segc = seg_codes(q + 1);
       {
         T ck[CKW];
 #pragma unroll
@@ -341,8 +362,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
         rec_store<T, CKW, true>(ckb + (size_t)q * 32 * CKW, lane, ck);
       }
       for (int u = 0; u < len; ++u) {
-        const int s = b + u;  // 0-based step index
-        const int cu = (t == 0 && s < n) ? (int)fa.hcode[hs + s] : kNull;
+        const int cu = (cur >> (3 * u)) & 7;
         T in3[3];
         wf_step<T, L, K, true, true, true>(st, cu, t, bnd, eps, tblE, ap, dl, zt, ei, in3);
       }
@@ -390,9 +410,21 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
     // lane 0's row above its strip (row 0 of the DP, or a pad row): S = K0 D(0, j)
     const T bndS = t == 0 ? bnd : (T)0;
 
+    // each lane's code at the start of segment qq (column b - t), and the first lane's codes
+    // of the segment's steps: loaded one segment ahead, as in phase A
+    auto seg_c0 = [&](int qq) {
+      if (qq < 0) return (int)kNull;
+      const int bb = qq < ramp ? qq : ramp + kSeg * (qq - ramp);
+      return hap_code_at(fa.hcode, hs, n, (int64_t)bb - t);
+    };
+    segc = seg_codes(nq - 1);
+    int segc0 = seg_c0(nq - 1);
     for (int q = nq - 1; q >= 0; --q) {
       const int b = q < ramp ? q : ramp + kSeg * (q - ramp);
       const int len = q < ramp ? 1 : kSeg;
+      const int cur = segc, cur0 = segc0;
+      segc = seg_codes(q - 1);
+      segc0 = seg_c0(q - 1);
       {
         T ck[CKW];
         rec_load<T, CKW, true>(ckb + (size_t)q * 32 * CKW, lane, ck);
@@ -409,17 +441,15 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
       }
       // bring the next (left) segment's checkpoint from DRAM towards L2 while this one runs
       if (q > 0 && lane == 0) prefetch_l2(ckb + (size_t)(q - 1) * 32 * CKW, 32 * CKW * sizeof(T));
-      st.c = hap_code_at(fa.hcode, hs, n, (int64_t)b - t);
+      st.c = cur0;
       T mxF = fmax(st.Md, st.Sd);
 #pragma unroll
       for (int r = 0; r < K; ++r) mxF = fmax(mxF, fmax(st.M[r], fmax(st.I[r], st.D[r])));
       // recompute the segment, recording the lane's rows after each step (column b+u2+1-t)
       // and the step's haplotype code (3 bits per step)
-      static_assert(3 * kSeg <= 31, "codes of a segment must fit one register");
       int codes = 0;
       for (int u2 = 0; u2 < len; ++u2) {
-        const int s = b + u2;
-        const int cu = (t == 0 && s < n) ? (int)fa.hcode[hs + s] : kNull;
+        const int cu = (cur >> (3 * u2)) & 7;
         T in3[3];
         wf_step<T, L, K, true, true, true>(st, cu, t, bnd, eps, tblE, ap, dl, zt, ei, in3);
         codes |= st.c << (3 * u2);
