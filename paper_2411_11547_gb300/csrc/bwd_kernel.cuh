@@ -126,11 +126,6 @@ __device__ __forceinline__ int bits_int(T x) {
   return (int)x;
 }
 
-__device__ __forceinline__ int hap_code_at(const uint8_t *hcode, int64_t hs, int64_t n,
-                                           int64_t j /* 1-based column */) {
-  return (j >= 1 && j <= n) ? (int)hcode[hs + j - 1] : kNull;
-}
-
 // Adjoint state of one lane.
 template <typename T, int K>
 struct AdjState {
@@ -321,19 +316,20 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
     T Sfin = 0;
     int Efin = 0;
     bool done = false;
-    // Haplotype codes of segment qq's steps, 3 bits per step (the first lane of a pair reads
-    // them; the others take theirs from the lane above).  Loaded one segment ahead, so the
-    // load latency stays off the steps' dependency chain.
+    // Haplotype codes of the lane's columns over segment qq's steps, 3 bits per step (at
+    // step s lane t is at column s + 1 - t; columns outside 1..n take the null code).  Every
+    // lane reads its own, one segment ahead: no code exchange and no load on the steps'
+    // dependency chain.  The reverse sweep reuses them.
     static_assert(3 * kSeg <= 31, "codes of a segment must fit one register");
     auto seg_codes = [&](int qq) {
       int cs = 0;
-      if (t == 0 && qq >= 0 && qq < nq) {
+      if (qq >= 0 && qq < nq) {
         const int bb = qq < ramp ? qq : ramp + kSeg * (qq - ramp);
         const int ll = qq < ramp ? 1 : kSeg;
 #pragma unroll
         for (int u = 0; u < kSeg; ++u) {
-          const int s = bb + u;
-          const int c = (u < ll && s < n) ? (int)fa.hcode[hs + s] : kNull;
+          const int64_t i = (int64_t)bb + u - t;  // 0-based haplotype position
+          const int c = (u < ll && i >= 0 && i < n) ? (int)fa.hcode[hs + i] : kNull;
           cs |= c << (3 * u);
         }
       }
@@ -364,7 +360,8 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
       for (int u = 0; u < len; ++u) {
         const int cu = (cur >> (3 * u)) & 7;
         T in3[3];
-        wf_step<T, L, K, true, true, true>(st, cu, t, bnd, eps, tblE, ap, dl, zt, ei, in3);
+        wf_step<T, L, K, true, true, true, false, true>(st, cu, t, bnd, eps, tblE, ap, dl, zt,
+                                                        ei, in3);
       }
       if (!done && b + len >= fin) {
         Sfin = st.acc;
@@ -410,21 +407,13 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
     // lane 0's row above its strip (row 0 of the DP, or a pad row): S = K0 D(0, j)
     const T bndS = t == 0 ? bnd : (T)0;
 
-    // each lane's code at the start of segment qq (column b - t), and the first lane's codes
-    // of the segment's steps: loaded one segment ahead, as in phase A
-    auto seg_c0 = [&](int qq) {
-      if (qq < 0) return (int)kNull;
-      const int bb = qq < ramp ? qq : ramp + kSeg * (qq - ramp);
-      return hap_code_at(fa.hcode, hs, n, (int64_t)bb - t);
-    };
+    // the lanes' codes of each segment's steps, loaded one segment ahead as in phase A
     segc = seg_codes(nq - 1);
-    int segc0 = seg_c0(nq - 1);
     for (int q = nq - 1; q >= 0; --q) {
       const int b = q < ramp ? q : ramp + kSeg * (q - ramp);
       const int len = q < ramp ? 1 : kSeg;
-      const int cur = segc, cur0 = segc0;
+      const int codes = segc;
       segc = seg_codes(q - 1);
-      segc0 = seg_c0(q - 1);
       {
         T ck[CKW];
         rec_load<T, CKW, true>(ckb + (size_t)q * 32 * CKW, lane, ck);
@@ -441,18 +430,15 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
       }
       // bring the next (left) segment's checkpoint from DRAM towards L2 while this one runs
       if (q > 0 && lane == 0) prefetch_l2(ckb + (size_t)(q - 1) * 32 * CKW, 32 * CKW * sizeof(T));
-      st.c = cur0;
       T mxF = fmax(st.Md, st.Sd);
 #pragma unroll
       for (int r = 0; r < K; ++r) mxF = fmax(mxF, fmax(st.M[r], fmax(st.I[r], st.D[r])));
       // recompute the segment, recording the lane's rows after each step (column b+u2+1-t)
-      // and the step's haplotype code (3 bits per step)
-      int codes = 0;
       for (int u2 = 0; u2 < len; ++u2) {
-        const int cu = (cur >> (3 * u2)) & 7;
+        const int cu = (codes >> (3 * u2)) & 7;
         T in3[3];
-        wf_step<T, L, K, true, true, true>(st, cu, t, bnd, eps, tblE, ap, dl, zt, ei, in3);
-        codes |= st.c << (3 * u2);
+        wf_step<T, L, K, true, true, true, false, true>(st, cu, t, bnd, eps, tblE, ap, dl, zt,
+                                                        ei, in3);
         if (u2 < len - 1) {  // the last step's state stays in registers
           T rec[RW];
 #pragma unroll

@@ -176,16 +176,21 @@ struct WfState {
 // recurrence uses their magnitudes (a free operand modifier).
 // TOP: lane 0 takes the row above its strip from (tM, tI, tT), already in its own scale,
 // instead of the DP's row 0 (row tiles of long reads: the previous tile's last row).
+// OWN: every lane passes the haplotype code of its own column in `cu` (no code exchange).
 template <typename T, int L, int K, bool EXT, bool PRIMED = false, bool ABS_E = false,
-          bool TOP = false>
+          bool TOP = false, bool OWN = false>
 __device__ __forceinline__ void wf_step(WfState<T, K> &st, int cu, int t, T bnd, T eps,
                                         const T *tbl, const T (&ap)[K], const T (&dl)[K],
                                         const T (&zt)[K], const T (&ei)[K], T (&in3)[3],
                                         T tM = 0, T tI = 0, T tT = 0) {
   constexpr unsigned FULL = 0xffffffffu;
   constexpr int CS = TableGeom<T, K>::CS;
-  const int cin = __shfl_up_sync(FULL, st.c, 1, L);
-  st.c = (t == 0) ? cu : cin;
+  if constexpr (OWN) {
+    st.c = cu;
+  } else {
+    const int cin = __shfl_up_sync(FULL, st.c, 1, L);
+    st.c = (t == 0) ? cu : cin;
+  }
   const T third = PRIMED ? st.I[K - 1] + zt[K - 1] * st.D[K - 1] : st.D[K - 1];
   T inM = __shfl_up_sync(FULL, st.M[K - 1], 1, L);
   T inI = __shfl_up_sync(FULL, st.I[K - 1], 1, L);
