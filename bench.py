@@ -39,9 +39,9 @@ FWD_OPS_PER_CELL = 6
 # 2; Q: I+D, alpha' M + S, w M^ G: 3; delta, zeta: 2; eps: 2): 6 + 6 + 9 + 1 = 22.
 BWD_OPS_PER_CELL = 22
 # DRAM bytes per cell of the adjoint kernel (read + written: its checkpoints), from an ncu
-# capture of wf_backward<float,16,10> on the 4.5e9-cell c3_grad batch (10.45 GB read, 13.73 GB
+# capture of wf_backward<float,16,10> on the 4.5e9-cell c3_grad batch (10.41 GB read, 13.73 GB
 # written); the c4 step's traffic is this times its cells.
-BWD_DRAM_BYTES_PER_CELL = (10.447 + 13.734) * 1e9 / 4.5e9
+BWD_DRAM_BYTES_PER_CELL = (10.413 + 13.734) * 1e9 / 4.5e9
 
 WORKLOAD_DESC = {
     "c4_persistent": "65,536 regions x 4 haplotypes x 16 reads = 2^22 pairs; read length "
