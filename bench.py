@@ -236,7 +236,14 @@ def main():
     out, flags = plan.forward()
     rescued = float((flags & phmm.FLAG_RESCUED64).ne(0).float().mean().item())
 
+    # one training step: the fused forward (log10 L of every pair and its partials from the
+    # adjoint sweep) and the FP64 per-read reduction weighted by dL
     def step():
+        plan.forward_partials(out, flags)
+        return plan.backward_partials(dL)
+
+    # the same step as two independent calls: the forward graph, then the whole backward
+    def step_two_call():
         plan.forward(out, flags)
         return plan.backward(dL)
 
@@ -265,6 +272,17 @@ def main():
         adj_ms.append(a)
         red_ms.append(r)
     launches = plan.launch_count(0) + plan.launch_count(1)
+
+    # the two-call step, timed the same way
+    for _ in range(2):
+        step_two_call()
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step_two_call()
+    e1.record(stream)
+    barrier()
+    ms_two = e0.elapsed_time(e1) / args.steps
 
     # forward alone (graph replay), timed the same way
     barrier()
@@ -333,7 +351,8 @@ def main():
     dfma = phmm.probe_pipe(2, 400)[0]
 
     # end to end through the public API with host buffers (pinned), every step:
-    # H2D of the batch, plan (validation), forward, adjoint, D2H of log10 L and gradients
+    # H2D of the batch, plan (validation), fused forward with partials, reduction, D2H of
+    # log10 L and the gradients
     e2e = None
     if not args.no_e2e:
         hb = {k: (torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
@@ -357,8 +376,8 @@ def main():
             db.gcp = float(batch["gcp"])
             db.alpha_mode = 0
             pl = phmm.Plan(db, opts)
-            o, _ = pl.forward()
-            gb, gi, gd, gg = pl.backward(dL)
+            o, _ = pl.forward_partials()
+            gb, gi, gd, gg = pl.backward_partials(dL)
             out_h.copy_(o, non_blocking=True)
             g_h[:sum_m].copy_(gb, non_blocking=True)
             g_h[sum_m:2 * sum_m].copy_(gi, non_blocking=True)
@@ -405,9 +424,9 @@ def main():
 
     # max over ranks of the step time
     if dist is not None:
-        t = torch.tensor([ms, ms_fwd, e2e["ms_per_step"] if e2e else 0.0], device=dev)
+        t = torch.tensor([ms, ms_fwd, e2e["ms_per_step"] if e2e else 0.0, ms_two], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_fwd = float(t[0]), float(t[1])
+        ms, ms_fwd, ms_two = float(t[0]), float(t[1]), float(t[3])
         if e2e:
             e2e["ms_per_step"] = float(t[2])
     total_cells = cells * ws
@@ -435,7 +454,11 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {WORKLOAD_DESC[args.workload]}",
-                   "pairs": P * ws, "cells": total_cells, "step": "forward + adjoint",
+                   "pairs": P * ws, "cells": total_cells,
+                   "step": ("log10 L and d(loss)/d(quals, gcp) of every pair with dL = 1: "
+                            "phmm_forward_partials (the adjoint sweep's own forward gives "
+                            "log10 L; pairs it cannot represent finished in FP64) + "
+                            "phmm_backward_partials (FP64 per-read reduction weighted by dL)"),
                    "first_line": "FP32 with per-lane exponents (FP64 rescue when unrepresentable)",
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"weak x{ws}",
                    "group_tables": ("built-in" if args.no_tune else
@@ -443,6 +466,8 @@ def main():
                                     f"range, {t_tune:.2f} s, outside the timed region)"),
                    "warps_per_block": {"forward": int(opts.warps_per_block),
                                        "adjoint": int(opts.bwd_warps_per_block)}},
+        "two_call_step": {"calls": "phmm_forward (graph) + phmm_backward",
+                          "ms_per_step": ms_two, "gcups": total_cells / (ms_two * 1e-3) / 1e9},
         "fwd_gcups": fwd_gcups,
         "fwd_wavefront_gcups": cells / (wf * 1e-3) / 1e9,
         "fwd_rescue_ms": statistics.median(resc_ms),
@@ -464,7 +489,8 @@ def main():
                      "unit": "T FP32 lane-ops/s", "frac": achieved / peak,
                      "traffic": cells * BWD_DRAM_BYTES_PER_CELL if dom_bwd else None,
                      "traffic_source": ("ncu dram__bytes_read+write of the adjoint on c3_grad "
-                                        "(5.37 B/cell), scaled by this step's cells"
+                                        f"({BWD_DRAM_BYTES_PER_CELL:.2f} B/cell), scaled by this "
+                                        "step's cells"
                                         if dom_bwd else None)},
         "gpu_launches": launches * args.steps,
         "clocks": sample_clk,

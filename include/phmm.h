@@ -154,6 +154,31 @@ int phmm_backward(phmm_plan *plan, void *ws, size_t ws_bytes, const double *dL,
                   float *d_base_q, float *d_ins_q, float *d_del_q, double *d_gcp,
                   void *stream);
 
+/*
+ * Fused training step, part 1: the adjoint sweep with dL = 1 for every pair.  Its own forward
+ * pass (the per-lane-exponent FP32 recurrence of Eq. 1-3; pairs it cannot represent finished
+ * in FP64) writes out_log10 / out_flags exactly as phmm_forward documents them (flags
+ * PHMM_FLAG_FP32 or PHMM_FLAG_RESCUED64, with PHMM_FLAG_EXTENDED), and every pair's
+ * d log10 L_p / d(Phred inputs) stays in ws.  A pair's gradient is linear in dL[p], so
+ * phmm_backward_partials then only weights and reduces them: one forward sweep per step
+ * instead of phmm_forward's plus the adjoint's.  Same arguments, ownership and errors as
+ * phmm_forward, plus PHMM_ETOOLONG for plans holding reads longer than PHMM_MAX_READ_LEN.
+ * Asynchronous on `stream`.
+ */
+int phmm_forward_partials(phmm_plan *plan, void *ws, size_t ws_bytes, double *out_log10,
+                          uint8_t *out_flags, void *stream);
+
+/*
+ * Fused training step, part 2: writes d_base_q, d_ins_q, d_del_q and d_gcp as phmm_backward
+ * does, from the partials the latest phmm_forward_partials on this plan and ws left there,
+ * each pair's weighted by dL[p] (device double [P]) in the FP64 per-read reduction.  May be
+ * called again with another dL.  PHMM_ESTATE without a preceding phmm_forward_partials, or
+ * after a phmm_backward (which overwrites the partials).  Asynchronous on `stream`.
+ */
+int phmm_backward_partials(phmm_plan *plan, void *ws, size_t ws_bytes, const double *dL,
+                           float *d_base_q, float *d_ins_q, float *d_del_q, double *d_gcp,
+                           void *stream);
+
 void phmm_plan_destroy(phmm_plan *plan);
 
 const char *phmm_status_str(int status);

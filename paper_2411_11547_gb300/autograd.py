@@ -19,7 +19,10 @@ class PairHMMLogLik(torch.autograd.Function):
     float64/float32 tensor `gcp`, and `layout`, a dict of device tensors with keys
     read_bases, read_off, hap_bases, hap_off, pair_read, pair_hap (and optionally
     alpha_mode).  Returns (log10L float64 [pairs], flags uint8 [pairs]); flags are not
-    differentiable.  One plan (validation, binning, workspace) is built per call.
+    differentiable.  One plan (validation, binning, workspace) is built per call.  When a
+    gradient is wanted the forward is the fused call (phmm_forward_partials: the adjoint sweep
+    yields log10 L and every pair's partials at once) and backward only weights the partials
+    by dy and reduces them; otherwise it is the plain forward.
     """
 
     @staticmethod
@@ -31,7 +34,8 @@ class PairHMMLogLik(torch.autograd.Function):
             layout["hap_off"], layout["pair_read"], layout["pair_hap"], g,
             layout.get("alpha_mode", 0))
         plan = _ph.Plan(db, opts)
-        out, flags = plan.forward()
+        ctx.fused = any(ctx.needs_input_grad[:4])
+        out, flags = plan.forward_partials() if ctx.fused else plan.forward()
         ctx.plan = plan
         ctx.gcp_like = gcp if torch.is_tensor(gcp) else None
         ctx.mark_non_differentiable(flags)
@@ -42,7 +46,8 @@ class PairHMMLogLik(torch.autograd.Function):
         plan = ctx.plan
         if dy is None:
             return None, None, None, None, None, None
-        dbq, diq, ddq, dgcp = plan.backward(dy.contiguous())
+        dy = dy.contiguous()
+        dbq, diq, ddq, dgcp = plan.backward_partials(dy) if ctx.fused else plan.backward(dy)
         gg = None
         if ctx.gcp_like is not None and ctx.needs_input_grad[3]:
             gg = dgcp.reshape(ctx.gcp_like.shape).to(ctx.gcp_like.dtype)

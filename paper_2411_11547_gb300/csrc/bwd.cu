@@ -66,8 +66,8 @@ int launch_binning(const phmm_batch &b, const CfgTable &tab, int32_t *key, int32
 int pair_offsets(const phmm_batch &b, char *scratch, int64_t **poff, cudaStream_t s);
 int reduce_gradients(const phmm_batch &b, char *scratch, const float *part_bq,
                      const float *part_iq, const float *part_dq, const double *pair_dgcp,
-                     float *dbq, float *diq, float *ddq, double *dgcp, cudaStream_t s,
-                     int *launches);
+                     const double *dL, float *dbq, float *diq, float *ddq, double *dgcp,
+                     cudaStream_t s, int *launches);
 size_t reduce_scratch_bytes_aligned(int64_t P, int64_t R);
 
 // ------------------------------------------------------------------------ host side ------
@@ -179,11 +179,12 @@ size_t bwd_workspace_bytes(const phmm_plan *pl) { return bwd_layout(pl).total; }
     if (rc_) return rc_;                \
   } while (0)
 
-// returns a cudaError_t value (0 on success)
-// ev3: events recorded before the adjoint kernels, after them, and after the reduction.
-int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, float *diq,
-                     float *ddq, double *dgcp, cudaStream_t s, int *launches,
-                     cudaEvent_t *ev3) {
+// The adjoint sweep over every pair: per-pair partials (times dL[p], or of log10 L itself
+// when dL is null) into the workspace, and with `out` non-null log10 L and flags from the
+// sweep's own forward pass.  Returns a cudaError_t value (0 on success).
+// ev2: events recorded before and after the adjoint kernels.
+int bwd_sweep_impl(phmm_plan *pl, char *ws, const double *dL, double *out, uint8_t *oflags,
+                   cudaStream_t s, int *launches, cudaEvent_t *ev2) {
   const phmm_batch &b = plan_batch(pl);
   const phmm_options &o = plan_options(pl);
   const BwdLayout Lo = bwd_layout(pl);
@@ -234,6 +235,8 @@ int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, floa
     f.beta64 = 1.0 - eps64;
     f.persistent = 1;
     a.dL = dL;
+    a.out = out;
+    a.oflags = oflags;
     a.poff = poff;
     a.part_bq = part_bq;
     a.part_iq = part_iq;
@@ -249,7 +252,7 @@ int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, floa
     a.why = (int32_t *)(ws + plan_layout_bin(pl, 10));
     CKB(cudaMemsetAsync(a.why, 0, 16, s));
     const int64_t nmax = plan_n_max(pl);
-    CKB(cudaEventRecord(ev3[0], s));
+    CKB(cudaEventRecord(ev2[0], s));
     for (int cfg : plan_bwd_used(pl)) {
       const int L = cfg_lanes(cfg), K = cfg_rows(cfg);
       BwdArgs c = a;
@@ -289,13 +292,34 @@ int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, floa
       ++*launches;
     }
   } else {
-    CKB(cudaEventRecord(ev3[0], s));
+    CKB(cudaEventRecord(ev2[0], s));
   }
-  CKB(cudaEventRecord(ev3[1], s));
-  CKB(reduce_gradients(b, red, part_bq, part_iq, part_dq, pdg, dbq, diq, ddq, dgcp, s,
-                       launches));
-  CKB(cudaEventRecord(ev3[2], s));
+  CKB(cudaEventRecord(ev2[1], s));
   return 0;
+}
+
+// The per-read FP64 reduction of the partials the latest sweep left in the workspace, each
+// pair's weighted by dL[p] when given.  ev1: event recorded after it.
+int bwd_reduce_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, float *diq,
+                    float *ddq, double *dgcp, cudaStream_t s, int *launches, cudaEvent_t ev1) {
+  const phmm_batch &b = plan_batch(pl);
+  const BwdLayout Lo = bwd_layout(pl);
+  char *bw = ws + plan_bwd_offset(pl);
+  float *part = (float *)(bw + Lo.part);
+  const int64_t rows = plan_pair_rows(pl) + 1;
+  CKB(reduce_gradients(b, bw + Lo.red, part, part + rows, part + 2 * rows,
+                       (const double *)(bw + Lo.pdgcp), dL, dbq, diq, ddq, dgcp, s, launches));
+  CKB(cudaEventRecord(ev1, s));
+  return 0;
+}
+
+// The whole backward: sweep with the partials scaled by dL, then the reduction.
+// ev3: events recorded before the adjoint kernels, after them, and after the reduction.
+int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, float *diq,
+                     float *ddq, double *dgcp, cudaStream_t s, int *launches,
+                     cudaEvent_t *ev3) {
+  CKB(bwd_sweep_impl(pl, ws, dL, nullptr, nullptr, s, launches, ev3));
+  return bwd_reduce_impl(pl, ws, nullptr, dbq, diq, ddq, dgcp, s, launches, ev3[2]);
 }
 
 }  // namespace phmm

@@ -11,7 +11,9 @@ namespace phmm {
 
 struct BwdArgs {
   FwdArgs f;               // pair list, inputs and prepared parameters (as the forward)
-  const double *dL;        // d(loss)/d(log10 L_p)
+  const double *dL;        // d(loss)/d(log10 L_p); null: partials of log10 L_p itself
+  double *out;             // non-null: also write log10 L_p and its flags from the sweep's
+  uint8_t *oflags;         //   own forward pass (the fused forward-with-partials call)
   const int64_t *poff;     // partial-gradient offsets per pair
   float *part_bq, *part_iq, *part_dq;
   double *pair_dgcp;
@@ -648,6 +650,10 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
     // d ln L / d eps = gE - gS / beta (beta = 1 - eps); d eps / d gcp = -(ln 10 / 10) eps
     const T dgcp_l = -(gEs - gSs / beta) * eps * (T)0.1;
     if (!(fabs(dgcp_l) < (T)1e30)) hs_any = 1;
+    if (valid && bad && a.out && t == 0) {
+      a.out[p] = __longlong_as_double(0x7ff8000000000000ll);
+      a.oflags[p] = PHMM_FLAG_INVALID;
+    }
     if (valid && !bad) {
       const bool to_rescue = hs_any && !a.rescue;
       if (to_rescue) {
@@ -661,8 +667,16 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
           }
         }
       } else {
-        const double dy = a.dL[p];
+        const double dy = a.dL ? a.dL[p] : 1.0;
         const int64_t po = a.poff[p];
+        if (a.out && t == 0) {
+          // log10 L = log10(S) + (ES - kBias (K-1)) log10 2, as the forward's per-lane-exponent
+          // tier writes it
+          constexpr double LOG10_2 = 0.301029995663981195213738894724493027;
+          a.out[p] = log10((double)S) + (double)(ES - kBias * (K - 1)) * LOG10_2;
+          a.oflags[p] = (uint8_t)(sizeof(T) == 4 ? PHMM_FLAG_FP32 : PHMM_FLAG_RESCUED64) |
+                        (uint8_t)PHMM_FLAG_EXTENDED;
+        }
         const bool ok = !hs_any;
         const float nanv = __int_as_float(0x7fc00000);
 #pragma unroll

@@ -23,6 +23,10 @@ int launch_binning(const phmm_batch &b, const CfgTable &tab, int32_t *key, int32
 int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, float *diq,
                      float *ddq, double *dgcp, cudaStream_t s, int *launches,
                      cudaEvent_t *ev3);
+int bwd_sweep_impl(phmm_plan *pl, char *ws, const double *dL, double *out, uint8_t *oflags,
+                   cudaStream_t s, int *launches, cudaEvent_t *ev2);
+int bwd_reduce_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, float *diq,
+                    float *ddq, double *dgcp, cudaStream_t s, int *launches, cudaEvent_t ev1);
 size_t bwd_workspace_bytes(const phmm_plan *pl);
 int bwd_default_cfg(int m);
 int bwd_cfg_supported(int cfg);
@@ -143,9 +147,13 @@ struct phmm_plan {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t gexec = nullptr;
   void *g_ws = nullptr, *g_out = nullptr, *g_flags = nullptr;
-  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // forward: FP32 kernels start/end, rescue end; adjoint: start, end, reduction end;
+  // reduction start of the fused path
+  cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int red_from = 4;   // the event the latest reduction started after
   bool bwd_timed = false;
   bool fwd_done = false;
+  bool partials_done = false;  // the workspace holds the partials of log10 L (fused forward)
   bool timed = false;  // the latest forward recorded the timing events
   int launches_fwd = 0, launches_bwd = 0;
   void *bwd_state = nullptr;  // owned by the backward translation unit
@@ -358,7 +366,7 @@ int phmm_plan_create(const phmm_batch *batch, const phmm_options *opt, void *str
   make_layout(pl);
   pl->L.total = pl->L.bwd + bwd_workspace_bytes(pl);
   cudaError_t ce = cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking);
-  for (int i = 0; i < 6 && ce == cudaSuccess; ++i) ce = cudaEventCreate(&pl->ev[i]);
+  for (int i = 0; i < 7 && ce == cudaSuccess; ++i) ce = cudaEventCreate(&pl->ev[i]);
   if (ce != cudaSuccess) {
     phmm_plan_destroy(pl);
     return cuda_fail(ce);
@@ -388,6 +396,16 @@ void phmm_plan_destroy(phmm_plan *pl) {
 
 }  // extern "C"
 
+// Zeroed counters and the per-row parameters and codes every sweep reads.
+static int enqueue_prep(phmm_plan *pl, char *ws, cudaStream_t s, int *launches) {
+  const WsLayout &L = pl->L;
+  CK(cudaMemsetAsync(ws + L.zero, 0, L.zero_bytes, s));
+  const int rc = launch_prep(pl->b, pl->sum_m, pl->beta32, (RowParams *)(ws + L.rp),
+                             (uint8_t *)(ws + L.rcode), (uint8_t *)(ws + L.hcode), s, launches);
+  if (rc) return cuda_fail((cudaError_t)rc);
+  return PHMM_OK;
+}
+
 // The whole forward pass as a stream-ordered launch sequence (capturable).
 // `timed`: record the plan's events around the FP32 and rescue kernels (not under capture).
 static int enqueue_forward(phmm_plan *pl, char *ws, double *out, uint8_t *flags,
@@ -396,11 +414,10 @@ static int enqueue_forward(phmm_plan *pl, char *ws, double *out, uint8_t *flags,
   const phmm_batch &b = pl->b;
   const phmm_options &o = pl->o;
   int launches = 0;
-  CK(cudaMemsetAsync(ws + L.zero, 0, L.zero_bytes, s));
+  int rc = enqueue_prep(pl, ws, s, &launches);
+  if (rc) return rc;
   RowParams *rp = (RowParams *)(ws + L.rp);
   uint8_t *rcode = (uint8_t *)(ws + L.rcode), *hcode = (uint8_t *)(ws + L.hcode);
-  int rc = launch_prep(b, pl->sum_m, pl->beta32, rp, rcode, hcode, s, &launches);
-  if (rc) return cuda_fail((cudaError_t)rc);
   int32_t *order = (int32_t *)(ws + L.order);
   int32_t *grp_begin = (int32_t *)(ws + L.grp_begin), *grp_count = (int32_t *)(ws + L.grp_count);
   if (o.binning && b.n_pairs > 0) {
@@ -566,8 +583,53 @@ int phmm_backward(phmm_plan *pl, void *ws, size_t ws_bytes, const double *dL, fl
   (void)cudaGetLastError();
   int launches = 0;
   pl->bwd_timed = false;
+  pl->partials_done = false;  // the sweep overwrites the partials with scaled ones
+  pl->red_from = 4;
   int rc = bwd_enqueue_impl(pl, (char *)ws, dL, dbq, diq, ddq, dgcp, (cudaStream_t)stream,
                             &launches, pl->ev + 3);
+  pl->launches_bwd = launches;
+  if (rc) return cuda_fail((cudaError_t)rc);
+  pl->bwd_timed = true;
+  return PHMM_OK;
+}
+
+int phmm_forward_partials(phmm_plan *pl, void *ws, size_t ws_bytes, double *out,
+                          uint8_t *flags, void *stream) {
+  const phmm::NvtxRange nvtx("phmm_forward_partials");
+  if (!pl || !ws || (pl->b.n_pairs > 0 && (!out || !flags))) return PHMM_EINVAL;
+  if (((uintptr_t)ws & 255) != 0) return PHMM_EINVAL;
+  if (ws_bytes < pl->L.total) return PHMM_ENOMEM;
+  if (pl->max_m > PHMM_MAX_READ_LEN) return PHMM_ETOOLONG;
+  cudaStream_t s = (cudaStream_t)stream;
+  (void)cudaGetLastError();
+  pl->bwd_timed = false;
+  pl->partials_done = false;
+  int launches = 0;
+  int rc = enqueue_prep(pl, (char *)ws, s, &launches);
+  if (rc) return rc;
+  rc = bwd_sweep_impl(pl, (char *)ws, nullptr, out, flags, s, &launches, pl->ev + 3);
+  pl->launches_fwd = launches;
+  if (rc) return cuda_fail((cudaError_t)rc);
+  pl->fwd_done = true;
+  pl->partials_done = true;
+  return PHMM_OK;
+}
+
+int phmm_backward_partials(phmm_plan *pl, void *ws, size_t ws_bytes, const double *dL,
+                           float *dbq, float *diq, float *ddq, double *dgcp, void *stream) {
+  const phmm::NvtxRange nvtx("phmm_backward_partials");
+  if (!pl || !ws || !dgcp) return PHMM_EINVAL;
+  if (pl->sum_m > 0 && (!dbq || !diq || !ddq)) return PHMM_EINVAL;
+  if (pl->b.n_pairs > 0 && !dL) return PHMM_EINVAL;
+  if (((uintptr_t)ws & 255) != 0) return PHMM_EINVAL;
+  if (ws_bytes < pl->L.total) return PHMM_ENOMEM;
+  if (!pl->partials_done) return PHMM_ESTATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  (void)cudaGetLastError();
+  int launches = 0;
+  pl->red_from = 6;
+  CK(cudaEventRecord(pl->ev[6], s));
+  const int rc = bwd_reduce_impl(pl, (char *)ws, dL, dbq, diq, ddq, dgcp, s, &launches, pl->ev[5]);
   pl->launches_bwd = launches;
   if (rc) return cuda_fail((cudaError_t)rc);
   pl->bwd_timed = true;
@@ -621,7 +683,7 @@ int phmm_plan_backward_ms(phmm_plan *pl, float *ms_adjoint, float *ms_reduce) {
   float a = -1.f, r = -1.f;
   if (pl->bwd_timed && cudaEventQuery(pl->ev[5]) == cudaSuccess) {
     if (cudaEventElapsedTime(&a, pl->ev[3], pl->ev[4]) != cudaSuccess) a = -1.f;
-    if (cudaEventElapsedTime(&r, pl->ev[4], pl->ev[5]) != cudaSuccess) r = -1.f;
+    if (cudaEventElapsedTime(&r, pl->ev[pl->red_from], pl->ev[5]) != cudaSuccess) r = -1.f;
   }
   if (ms_adjoint) *ms_adjoint = a;
   if (ms_reduce) *ms_reduce = r;

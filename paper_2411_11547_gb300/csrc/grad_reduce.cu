@@ -120,11 +120,12 @@ __global__ void k_segment_sort(const int64_t *seg_off, int64_t R, const int32_t 
   }
 }
 
-// One warp per read: FP64 sum of the partials of its pairs, in pair order.
+// One warp per read: FP64 sum of the partials of its pairs, in pair order, each times
+// dL[pair] when dL is given (partials of log10 L itself), else as stored (already scaled).
 __global__ void k_read_reduce(const int64_t *read_off, int64_t R, const int64_t *seg_off,
                               const int32_t *sorted, const int64_t *poff, const float *part_bq,
-                              const float *part_iq, const float *part_dq, float *dbq,
-                              float *diq, float *ddq) {
+                              const float *part_iq, const float *part_dq, const double *dL,
+                              float *dbq, float *diq, float *ddq) {
   const int lane = threadIdx.x & 31;
   for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < R;
        r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
@@ -133,10 +134,12 @@ __global__ void k_read_reduce(const int64_t *read_off, int64_t R, const int64_t 
     for (int64_t i = lane; i < m; i += 32) {
       double sb = 0.0, si = 0.0, sd = 0.0;
       for (int64_t k = b; k < e; ++k) {
-        const int64_t o = poff[sorted[k]] + i;
-        sb += (double)part_bq[o];
-        si += (double)part_iq[o];
-        sd += (double)part_dq[o];
+        const int32_t pr = sorted[k];
+        const int64_t o = poff[pr] + i;
+        const double w = dL ? dL[pr] : 1.0;
+        sb += w * (double)part_bq[o];
+        si += w * (double)part_iq[o];
+        sd += w * (double)part_dq[o];
       }
       dbq[r0 + i] = (float)sb;
       diq[r0 + i] = (float)si;
@@ -147,11 +150,12 @@ __global__ void k_read_reduce(const int64_t *read_off, int64_t R, const int64_t 
 
 // Fixed-shape FP64 sum of P values: kSumBlocks block partials, then one block.
 constexpr int kSumBlocks = 256;
-__global__ void __launch_bounds__(256) k_sum_stage1(const double *x, int64_t P, double *part) {
+__global__ void __launch_bounds__(256) k_sum_stage1(const double *x, const double *w, int64_t P,
+                                                    double *part) {
   __shared__ double sh[256];
   double s = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)256 + threadIdx.x; i < P; i += (int64_t)kSumBlocks * 256)
-    s += x[i];
+    s += w ? w[i] * x[i] : x[i];
   sh[threadIdx.x] = s;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
@@ -232,11 +236,12 @@ int pair_offsets(const phmm_batch &b, char *scratch, int64_t **poff, cudaStream_
   return (int)cudaGetLastError();
 }
 
-// Per-read FP64 reduction of the pair partials and the FP64 sum of per-pair d/dgcp.
+// Per-read FP64 reduction of the pair partials and the FP64 sum of per-pair d/dgcp; with
+// dL non-null the per-pair values are partials of log10 L, weighted by dL[p] in FP64.
 int reduce_gradients(const phmm_batch &b, char *scratch, const float *part_bq,
                      const float *part_iq, const float *part_dq, const double *pair_dgcp,
-                     float *dbq, float *diq, float *ddq, double *dgcp, cudaStream_t s,
-                     int *launches) {
+                     const double *dL, float *dbq, float *diq, float *ddq, double *dgcp,
+                     cudaStream_t s, int *launches) {
   ReduceScratch rs = carve(scratch, b.n_pairs, b.n_reads);
   const int64_t P = b.n_pairs, R = b.n_reads;
   cudaMemsetAsync(rs.cnt, 0, 8 * (size_t)(R + 1), s);
@@ -250,9 +255,9 @@ int reduce_gradients(const phmm_batch &b, char *scratch, const float *part_bq,
     k_segment_sort<<<grid_for(R * 32, 256), 256, 0, s>>>(rs.seg_off, R, rs.seg, rs.sorted);
   }
   k_read_reduce<<<grid_for(R * 32, 256), 256, 0, s>>>(b.read_off, R, rs.seg_off, rs.sorted,
-                                                      rs.poff, part_bq, part_iq, part_dq, dbq,
-                                                      diq, ddq);
-  k_sum_stage1<<<kSumBlocks, 256, 0, s>>>(pair_dgcp, P, rs.sum_part);
+                                                      rs.poff, part_bq, part_iq, part_dq, dL,
+                                                      dbq, diq, ddq);
+  k_sum_stage1<<<kSumBlocks, 256, 0, s>>>(pair_dgcp, dL, P, rs.sum_part);
   k_sum_stage2<<<1, 256, 0, s>>>(rs.sum_part, dgcp);
   *launches += 8;
   return (int)cudaGetLastError();

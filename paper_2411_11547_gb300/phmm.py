@@ -80,6 +80,10 @@ def lib():
             L.phmm_forward.restype = ctypes.c_int
             L.phmm_backward.argtypes = [vp, vp, ctypes.c_size_t, vp, vp, vp, vp, vp, vp]
             L.phmm_backward.restype = ctypes.c_int
+            L.phmm_forward_partials.argtypes = [vp, vp, ctypes.c_size_t, vp, vp, vp]
+            L.phmm_forward_partials.restype = ctypes.c_int
+            L.phmm_backward_partials.argtypes = [vp, vp, ctypes.c_size_t, vp, vp, vp, vp, vp, vp]
+            L.phmm_backward_partials.restype = ctypes.c_int
             L.phmm_plan_destroy.argtypes = [vp]
             L.phmm_plan_destroy.restype = None
             L.phmm_status_str.argtypes = [ctypes.c_int]
@@ -256,6 +260,34 @@ class Plan:
         return out, flags
 
     def backward(self, dL, stream=None):
+        """phmm_backward: d(loss)/d(quals) given dL = d(loss)/d(log10 L) (after forward)."""
+        return self._grad(lib().phmm_backward, "phmm_backward", dL, stream)
+
+    def forward_partials(self, out=None, flags=None, stream=None):
+        """phmm_forward_partials: log10 L and flags from the adjoint sweep's own forward pass,
+        keeping every pair's d log10 L / d(quals) in the workspace for backward_partials."""
+        import torch
+        P = self.dbatch.n_pairs
+        dev = self.dbatch.read_bases.device
+        if out is None:
+            out = torch.empty(P, dtype=torch.float64, device=dev)
+        if flags is None:
+            flags = torch.empty(P, dtype=torch.uint8, device=dev)
+        rc = lib().phmm_forward_partials(self.handle, ctypes.c_void_p(self._ws_ptr),
+                                         self.ws_bytes,
+                                         ctypes.c_void_p(out.data_ptr() if P else 0),
+                                         ctypes.c_void_p(flags.data_ptr() if P else 0),
+                                         _stream(stream))
+        if rc != PHMM_OK:
+            raise PhmmError(rc, "phmm_forward_partials")
+        return out, flags
+
+    def backward_partials(self, dL, stream=None):
+        """phmm_backward_partials: the partials of the latest forward_partials weighted by dL
+        and reduced per read (same outputs as backward)."""
+        return self._grad(lib().phmm_backward_partials, "phmm_backward_partials", dL, stream)
+
+    def _grad(self, fn, name, dL, stream):
         import torch
         dev = self.dbatch.read_bases.device
         tot = max(self.sum_m, 1)
@@ -264,12 +296,12 @@ class Plan:
         ddq = torch.empty(tot, dtype=torch.float32, device=dev)
         dgcp = torch.empty(1, dtype=torch.float64, device=dev)
         dL = dL.to(device=dev, dtype=torch.float64).contiguous()
-        rc = lib().phmm_backward(self.handle, ctypes.c_void_p(self._ws_ptr), self.ws_bytes,
-                                 ctypes.c_void_p(dL.data_ptr()), ctypes.c_void_p(dbq.data_ptr()),
-                                 ctypes.c_void_p(diq.data_ptr()), ctypes.c_void_p(ddq.data_ptr()),
-                                 ctypes.c_void_p(dgcp.data_ptr()), _stream(stream))
+        rc = fn(self.handle, ctypes.c_void_p(self._ws_ptr), self.ws_bytes,
+                ctypes.c_void_p(dL.data_ptr()), ctypes.c_void_p(dbq.data_ptr()),
+                ctypes.c_void_p(diq.data_ptr()), ctypes.c_void_p(ddq.data_ptr()),
+                ctypes.c_void_p(dgcp.data_ptr()), _stream(stream))
         if rc != PHMM_OK:
-            raise PhmmError(rc, "phmm_backward")
+            raise PhmmError(rc, name)
         return dbq[: self.sum_m], diq[: self.sum_m], ddq[: self.sum_m], dgcp
 
     def launch_count(self, which=0):

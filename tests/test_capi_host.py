@@ -31,7 +31,8 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ("phmm_plan_create", "phmm_forward", "phmm_backward", "phmm_workspace_bytes",
-                 "phmm_plan_destroy", "phmm_status_str"):
+                 "phmm_forward_partials", "phmm_backward_partials", "phmm_plan_destroy",
+                 "phmm_status_str"):
         assert must in names
 
 
@@ -69,6 +70,9 @@ def test_forward_rejects_null_plan(lib):
     from paper_2411_11547_gb300 import phmm
     assert lib.phmm_forward(None, None, 0, None, None, None) == phmm.PHMM_EINVAL
     assert lib.phmm_backward(None, None, 0, None, None, None, None, None, None) == phmm.PHMM_EINVAL
+    assert lib.phmm_forward_partials(None, None, 0, None, None, None) == phmm.PHMM_EINVAL
+    assert lib.phmm_backward_partials(None, None, 0, None, None, None, None, None,
+                                      None) == phmm.PHMM_EINVAL
     assert lib.phmm_workspace_bytes(None) == 0
 
 

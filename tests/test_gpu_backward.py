@@ -38,23 +38,34 @@ def grad_close(got, want, name):
                              f" got {got[i]:.6g} want {want[i]:.6g}")
 
 
-def run_grad(ph, batch, dy, **opt):
+def run_grad(ph, batch, dy, fused=False, **opt):
+    """log10 L, gradients and flags through phmm_forward + phmm_backward, or (fused) through
+    phmm_forward_partials + phmm_backward_partials."""
     import torch
     plan = ph.Plan(ph.DeviceBatch(batch), ph.options(**opt))
-    out, flags = plan.forward()
-    gb, gi, gd, gg = plan.backward(torch.as_tensor(dy, dtype=torch.float64, device="cuda"))
+    out, flags = plan.forward_partials() if fused else plan.forward()
+    dyt = torch.as_tensor(dy, dtype=torch.float64, device="cuda")
+    gb, gi, gd, gg = plan.backward_partials(dyt) if fused else plan.backward(dyt)
     torch.cuda.synchronize()
     return (out.cpu().numpy(), gb.cpu().numpy(), gi.cpu().numpy(), gd.cpu().numpy(),
-            float(gg.cpu().numpy()[0]), plan)
+            float(gg.cpu().numpy()[0]), plan, flags.cpu().numpy())
 
 
 def check_against_oracle(ph, b, dy, **opt):
-    y, gb, gi, gd, gg, plan = run_grad(ph, b, dy, **opt)
+    """Both the two-call path and the fused path against the oracle's log10 L (1e-3) and
+    adjoint (1e-3 relative)."""
     wy, wb, wi, wd, wg = oracle.backward_batch(b, dy)
-    grad_close(gb, wb, "d/dbq")
-    grad_close(gi, wi, "d/diq")
-    grad_close(gd, wd, "d/ddq")
-    assert abs(gg - wg) <= RTOL * abs(wg) + 1e-9, (gg, wg)
+    for fused in (False, True):
+        y, gb, gi, gd, gg, plan, fl = run_grad(ph, b, dy, fused=fused, **opt)
+        assert np.all(np.abs(y - wy) <= 1e-3), (fused, np.abs(y - wy).max())
+        if fused:
+            ext = (fl & ph.FLAG_EXTENDED) != 0
+            one = ((fl & ph.FLAG_FP32) != 0) ^ ((fl & ph.FLAG_RESCUED64) != 0)
+            assert np.all(ext & one & ((fl & ph.FLAG_INVALID) == 0)), np.unique(fl)
+        grad_close(gb, wb, f"d/dbq fused={fused}")
+        grad_close(gi, wi, f"d/diq fused={fused}")
+        grad_close(gd, wd, f"d/ddq fused={fused}")
+        assert abs(gg - wg) <= RTOL * abs(wg) + 1e-9, (fused, gg, wg)
 
 
 @pytest.mark.parametrize("seed", [0, 1])
@@ -105,6 +116,41 @@ def test_backward_requires_forward(phmm):
     with pytest.raises(phmm.PhmmError) as e:
         plan.backward(torch.ones(4, dtype=torch.float64, device="cuda"))
     assert e.value.status == phmm.PHMM_ESTATE
+    # the fused reduction needs the fused forward's partials, and phmm_backward replaces them
+    with pytest.raises(phmm.PhmmError) as e:
+        plan.backward_partials(torch.ones(4, dtype=torch.float64, device="cuda"))
+    assert e.value.status == phmm.PHMM_ESTATE
+    plan.forward_partials()
+    plan.backward_partials(torch.ones(4, dtype=torch.float64, device="cuda"))
+    plan.backward(torch.ones(4, dtype=torch.float64, device="cuda"))
+    with pytest.raises(phmm.PhmmError) as e:
+        plan.backward_partials(torch.ones(4, dtype=torch.float64, device="cuda"))
+    assert e.value.status == phmm.PHMM_ESTATE
+
+
+def test_fused_partials_are_linear_in_dL(phmm):
+    """The fused reduction weights fixed per-pair partials: gradients for dL1, dL2 and
+    dL1 + 3 dL2 from one phmm_forward_partials satisfy g(dL1 + 3 dL2) = g(dL1) + 3 g(dL2) up
+    to the final FP32 rounding, and equal the two-call path's for the same dL."""
+    import torch
+    b = synth.random_pairs(17, 90, (10, 200), (10, 300), related=0.5, qual_dtype=np.float32)
+    P = len(b["pair_read"])
+    rng = np.random.default_rng(3)
+    d1 = torch.as_tensor(rng.uniform(-1, 1, P), device="cuda")
+    d2 = torch.as_tensor(rng.uniform(-1, 1, P), device="cuda")
+    plan = phmm.Plan(phmm.DeviceBatch(b))
+    plan.forward_partials()
+    g1 = [x.double().cpu().numpy() for x in plan.backward_partials(d1)]
+    g2 = [x.double().cpu().numpy() for x in plan.backward_partials(d2)]
+    g3 = [x.double().cpu().numpy() for x in plan.backward_partials(d1 + 3 * d2)]
+    for a, c, s3 in zip(g1, g2, g3):
+        lin = a + 3 * c
+        assert np.allclose(s3, lin, rtol=1e-5, atol=1e-6 * np.abs(lin).max()), np.abs(s3 - lin).max()
+    two = phmm.Plan(phmm.DeviceBatch(b))
+    two.forward()
+    h = [x.double().cpu().numpy() for x in two.backward(d1 + 3 * d2)]
+    for a, c in zip(h, g3):
+        assert np.allclose(a, c, rtol=1e-5, atol=1e-6 * np.abs(a).max()), np.abs(a - c).max()
 
 
 def test_backward_deterministic(phmm):
@@ -113,10 +159,11 @@ def test_backward_deterministic(phmm):
     b = dict(b, base_q=b["base_q"].astype(np.float32), ins_q=b["ins_q"].astype(np.float32),
              del_q=b["del_q"].astype(np.float32))
     dy = np.random.default_rng(2).normal(size=len(b["pair_read"]))
-    r1 = run_grad(phmm, b, dy)
-    r2 = run_grad(phmm, b, dy)
-    for x, y in zip(r1[1:5], r2[1:5]):
-        assert np.array_equal(np.asarray(x), np.asarray(y))
+    for fused in (False, True):
+        r1 = run_grad(phmm, b, dy, fused=fused)
+        r2 = run_grad(phmm, b, dy, fused=fused)
+        for x, y in zip(r1[:5], r2[:5]):
+            assert np.array_equal(np.asarray(x), np.asarray(y))
 
 
 def test_reads_much_longer_than_haplotypes(phmm):
@@ -197,3 +244,10 @@ def test_c4_adjoint_full_size_sampled_regions(phmm):
     grad_close(gb[idx], wb[idx], "d/dbq")
     grad_close(gi[idx], wi[idx], "d/diq")
     grad_close(gd[idx], wd[idx], "d/ddq")
+    # the fused step on the same plan: log10 L of the sampled pairs and the same gradients
+    y, _ = plan.forward_partials()
+    fb, fi, fd, fg = plan.backward_partials(torch.as_tensor(dy, device="cuda"))
+    assert np.all(np.abs(y.cpu().numpy()[pairs] - wy) <= 1e-3)
+    grad_close(fb.cpu().numpy()[idx], wb[idx], "fused d/dbq")
+    grad_close(fi.cpu().numpy()[idx], wi[idx], "fused d/diq")
+    grad_close(fd.cpu().numpy()[idx], wd[idx], "fused d/ddq")
