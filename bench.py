@@ -38,6 +38,9 @@ FWD_OPS_PER_CELL = 6
 # recurrences (u = beta lambda M^: 1; M^: 3; I^: 1; D^: 1) plus the partials (alpha, beta:
 # 2; Q: I+D, alpha' M + S, w M^ G: 3; delta, zeta: 2; eps: 2): 6 + 6 + 9 + 1 = 22.
 BWD_OPS_PER_CELL = 22
+# subset size of the end-to-end host call (phmm_grad_host): with the ramp at both ends about 7
+# subsets on the 3e11-cell step (measured best of 2^33..2^37 on GB300)
+E2E_SUBSET_CELLS = 1 << 37
 # DRAM bytes per cell of the adjoint kernel (read + written: its checkpoints), from an ncu
 # capture of wf_backward<float,16,10> on the 4.5e9-cell c3_grad batch (10.41 GB read, 13.73 GB
 # written); the c4 step's traffic is this times its cells.
@@ -350,10 +353,37 @@ def main():
     ffma2 = phmm.probe_pipe(1, 4000)[0]
     dfma = phmm.probe_pipe(2, 400)[0]
 
-    # end to end through the public API with host buffers (pinned), every step:
-    # H2D of the batch, plan (validation), fused forward with partials, reduction, D2H of
-    # log10 L and the gradients
+    # end to end from host memory through phmm_grad_host, the library's call for a batch in
+    # host memory: every step packs the batch into pinned staging, copies it and dL = 1 to
+    # the device, runs the fused step per subset (plan with validation, forward with
+    # partials, weighted reduction) and copies log10 L, flags and the gradients back, the
+    # copies of one subset overlapping the computation of the previous one
     e2e = None
+    e2e_dev = None
+    if not args.no_e2e:
+        sum_m = int(batch["read_off"][-1])
+        dL_h = np.ones(P)
+        outs = (np.empty(P), np.empty(P, dtype=np.uint8), np.empty(sum_m, dtype=np.float32),
+                np.empty(sum_m, dtype=np.float32), np.empty(sum_m, dtype=np.float32))
+        h2d = sum(np.asarray(batch[k]).nbytes for k in
+                  ("read_bases", "base_q", "ins_q", "del_q", "read_off", "hap_bases", "hap_off",
+                   "pair_read", "pair_hap")) + dL_h.nbytes
+        d2h = sum(x.nbytes for x in outs) + 8
+        phmm.grad_host(batch, dL_h, opts, subset_cells=E2E_SUBSET_CELLS, out=outs)  # buffers
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            phmm.grad_host(batch, dL_h, opts, subset_cells=E2E_SUBSET_CELLS, out=outs)
+        barrier()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
+               "call": f"phmm_grad_host (host arrays in and out, subsets of "
+                       f"{E2E_SUBSET_CELLS:.3g} cells)"}
+        phmm.lib().phmm_score_host_release()
+
+    # the same through the device API, unpipelined: every step copies the batch from pinned
+    # host tensors, builds a plan, runs the fused step and copies the results back
     if not args.no_e2e:
         hb = {k: (torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
                   if isinstance(v, np.ndarray) else v) for k, v in batch.items()}
@@ -362,9 +392,6 @@ def main():
         sum_m = int(batch["read_off"][-1])
         g_h = torch.empty(3 * sum_m, dtype=torch.float32).pin_memory()
         d2h = out_h.numel() * 8 + g_h.numel() * 4 + 8
-
-        class _HostView:  # DeviceBatch from pinned host tensors, copied every step
-            pass
 
         def e2e_step():
             db = phmm.DeviceBatch.__new__(phmm.DeviceBatch)
@@ -391,9 +418,10 @@ def main():
         for _ in range(args.steps):
             e2e_step()
         barrier()
-        e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-        e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms, "_cells": cells}
+        e2e_dev = {"ms_per_step": (time.perf_counter() - t0) * 1e3 / args.steps,
+                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                   "call": "DeviceBatch from pinned tensors + Plan + forward_partials + "
+                           "backward_partials + copies back, one step at a time"}
 
     # end-to-end forward scoring from host memory (the host workflow of Sec. III-A) on the
     # NA12878-shaped stand-in of Table I: pipelined subsets, host packing and copies included
@@ -434,7 +462,8 @@ def main():
     fwd_gcups = total_cells / (ms_fwd * 1e-3) / 1e9
     if e2e:
         e2e["value"] = total_cells / (e2e["ms_per_step"] * 1e-3) / 1e9
-        e2e.pop("_cells")
+    if e2e_dev:
+        e2e_dev["value"] = total_cells / (e2e_dev["ms_per_step"] * 1e-3) / 1e9
 
     # roofline of the dominant kernel: the adjoint wavefront (FP32 pipe bound)
     peak = SMS * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12  # T lane-ops/s at the max SM clock
@@ -497,6 +526,8 @@ def main():
     }
     if e2e:
         line["e2e"] = e2e
+    if e2e_dev:
+        line["e2e_device_api"] = e2e_dev
     if hostpipe:
         line["host_pipeline_fwd"] = hostpipe
     if rank == 0 and not args.no_cpu_baseline:

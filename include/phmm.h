@@ -45,8 +45,9 @@ extern "C" {
 
 #define PHMM_MAX_READ_LEN 512 /* longest read (rows) one wavefront group holds */
 /* Longest read phmm_forward scores: reads beyond PHMM_MAX_READ_LEN are swept in row tiles of
- * PHMM_MAX_READ_LEN rows (Sec. III-C supports reads up to 1,024).  phmm_backward and
- * phmm_forward_noalloc take reads up to PHMM_MAX_READ_LEN only. */
+ * PHMM_MAX_READ_LEN rows (Sec. III-C supports reads up to 1,024).  phmm_backward,
+ * phmm_forward_partials, phmm_grad_host and phmm_forward_noalloc take reads up to
+ * PHMM_MAX_READ_LEN only. */
 #define PHMM_MAX_READ_LEN_FWD 2048
 
 /* ---- per-pair flags written by phmm_forward ---------------------------------------- */
@@ -239,7 +240,9 @@ int phmm_autotune(const phmm_batch *batch, phmm_options *opt, int which, int64_t
  * End-to-end scoring of a batch held in HOST memory (the host workflow of Sec. III-A:
  * partition, transfer, score, transfer back).  Every pointer of *host_batch is host memory
  * (pageable or pinned); out_log10 / out_flags are host arrays of n_pairs.  Pairs are grouped by
- * read and cut into subsets of about `subset_cells` cells (Eq. 5; at least one read each).
+ * read and cut into subsets of about `subset_cells` cells (Eq. 5; at least one read each;
+ * the first three subsets take 1/8, 1/4 and 1/2 of that, and the last ones halve what is left
+ * down to 1/8, so the transfers that cannot overlap any computation stay small).
  * Each subset is packed into pinned staging memory, copied to the device in one transfer,
  * validated and scored with phmm_plan_create / phmm_forward (options `opt`, NULL = defaults;
  * CUDA graphs are not used), and its results copied back, on one of two streams, so the host
@@ -253,6 +256,24 @@ int phmm_autotune(const phmm_batch *batch, phmm_options *opt, int which, int64_t
 int phmm_score_host(const phmm_batch *host_batch, const phmm_options *opt,
                     int64_t subset_cells, double *out_log10, uint8_t *out_flags);
 void phmm_score_host_release(void);
+
+/*
+ * The same pipeline for the gradient: given dL[p] = d(loss)/d(log10 L_p) in host memory
+ * (double [P]; known before the call, e.g. a fixed weighting of the log-likelihoods), every
+ * subset runs the fused step (phmm_forward_partials, then phmm_backward_partials with the
+ * subset's dL) and returns out_log10 / out_flags as phmm_score_host does, and
+ *   d_base_q, d_ins_q, d_del_q : host float [sum m], as phmm_backward (reads without pairs: 0);
+ *   d_gcp                      : host double [1], summed over the subsets in order.
+ * A subset holds every pair of its reads, so each read's gradient comes from one subset's
+ * FP64 reduction.  The copies of one subset overlap the computation of the previous one.
+ * Errors: those of phmm_score_host, PHMM_EINVAL for a NULL dL or gradient array,
+ * PHMM_ETOOLONG for reads longer than PHMM_MAX_READ_LEN.  Shares phmm_score_host's buffers
+ * and lock.
+ */
+int phmm_grad_host(const phmm_batch *host_batch, const phmm_options *opt,
+                   int64_t subset_cells, const double *dL, double *out_log10,
+                   uint8_t *out_flags, float *d_base_q, float *d_ins_q, float *d_del_q,
+                   double *d_gcp);
 
 /*
  * Forward scoring for callers that cannot allocate device memory.

@@ -33,6 +33,58 @@ int bwd_cfg_supported(int cfg);
 
 static thread_local int g_last_cuda = 0;
 
+// Result words of plan-time validation: kValidateSlots static 64-byte device slots, one per
+// plan creation in progress on this device (taken and given back under a lock); a creation
+// that finds every slot taken allocates its own.
+constexpr int kValidateSlots = 64;
+__device__ unsigned long long g_validate_slot[kValidateSlots][8];
+struct ValidateSlot {
+  static std::mutex &mu() {
+    static std::mutex m;
+    return m;
+  }
+  static uint64_t &busy(int dev) {  // bit i: slot i in use on device dev
+    static uint64_t b[64] = {};
+    return b[dev & 63];
+  }
+  int dev = 0, idx = -1;
+  void *p = nullptr;
+  cudaError_t err = cudaSuccess;
+  bool owned = false;
+  ValidateSlot() {
+    err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return;
+    {
+      std::lock_guard<std::mutex> lock(mu());
+      uint64_t &b = busy(dev);
+      for (int i = 0; i < kValidateSlots; ++i)
+        if (!(b >> i & 1)) {
+          b |= 1ull << i;
+          idx = i;
+          break;
+        }
+    }
+    if (idx >= 0) {
+      void *base = nullptr;
+      err = cudaGetSymbolAddress(&base, g_validate_slot);
+      if (err == cudaSuccess) p = (char *)base + (size_t)idx * 64;
+    } else {
+      err = cudaMalloc(&p, 64);
+      owned = err == cudaSuccess;
+      if (!owned) p = nullptr;
+    }
+  }
+  ~ValidateSlot() {
+    if (owned) cudaFree(p);
+    if (idx >= 0) {
+      std::lock_guard<std::mutex> lock(mu());
+      busy(dev) &= ~(1ull << idx);
+    }
+  }
+  void *ptr() const { return p; }
+  cudaError_t error() const { return err == cudaSuccess ? cudaErrorUnknown : err; }
+};
+
 static int cuda_fail(cudaError_t e) {
   g_last_cuda = (int)e;
   return PHMM_ECUDA;
@@ -302,9 +354,12 @@ int phmm_plan_create(const phmm_batch *batch, const phmm_options *opt, void *str
     if (ho[h + 1] - ho[h] <= 0 || ho[h + 1] - ho[h] > INT32_MAX / 2) return PHMM_EINVAL;
   const int64_t sum_m = ro[b.n_reads], sum_n = ho[b.n_haps];
 
-  // device checks: bases, Phred values, pair ids; and the cell count of Eq. 5
-  void *dbuf = nullptr;
-  CK(cudaMalloc(&dbuf, 64));
+  // device checks: bases, Phred values, pair ids; and the cell count of Eq. 5.  The result
+  // words live in a static device slot: cudaFree would wait for the whole device, stalling
+  // a caller that creates the next plan while another stream computes.
+  ValidateSlot vs;
+  void *dbuf = vs.ptr();
+  if (!dbuf) return cuda_fail(vs.error());
   CK(cudaMemsetAsync(dbuf, 0, 64, s));
   unsigned *err = (unsigned *)dbuf;
   unsigned long long *cells = (unsigned long long *)((char *)dbuf + 8);
@@ -312,7 +367,6 @@ int phmm_plan_create(const phmm_batch *batch, const phmm_options *opt, void *str
   unsigned long long hbuf[3] = {0, 0, 0};
   cudaError_t e2 = rc ? (cudaError_t)rc : cudaMemcpyAsync(hbuf, dbuf, 24, cudaMemcpyDeviceToHost, s);
   if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(s);
-  cudaFree(dbuf);
   if (e2 != cudaSuccess) return cuda_fail(e2);
   if ((unsigned)hbuf[0] != 0) return PHMM_EINVAL;
 

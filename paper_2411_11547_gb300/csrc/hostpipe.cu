@@ -1,6 +1,6 @@
 // End-to-end scoring of a batch held in host memory: the host workflow of Sec. III-A
 // (partition into subsets, transfer, score, transfer back), with the copies of one subset
-// overlapping the scoring of the previous one.
+// overlapping the scoring of the previous one; and the same pipeline for the gradient.
 //
 // Pairs are grouped by read (every pair of a read in one subset) and cut into subsets of
 // about `subset_cells` cells.  Per subset the host packs the reads, the haplotypes the pairs
@@ -8,7 +8,10 @@
 // one copy; the subset is then validated and scored through the library's own plan and
 // forward on one of two streams, and its log10 L and flags come back by one copy each.  While
 // the GPU scores subset k on one stream, the host packs subset k+1 and starts its copy on
-// the other.
+// the other.  In the gradient mode the subset's dL travels with its inputs, the plan runs the
+// fused step (forward with partials, then the reduction weighted by dL), and the subset's
+// per-read gradients come back with its results: a subset holds whole reads, so their
+// gradients are complete there, and the d/dgcp of the subsets are summed in subset order.
 #include <cuda_runtime.h>
 #include <algorithm>
 #include <cstdint>
@@ -38,8 +41,18 @@ struct Slot {
   std::vector<int64_t> pairs;      // global pair ids of the subset in flight (if scattered)
   bool contiguous = false;         // else: the pairs are p0 .. p0 + np - 1
   int64_t p0 = 0, np = 0;
+  int64_t b0 = 0, sm = 0;          // the subset's reads: bases b0 .. b0 + sm - 1
   size_t res_off = 0;              // offset of the results in dev / hres
+  size_t grad_off = 0;             // offset of the gradients within the results
   bool busy = false;
+};
+
+// Where a pipeline call writes (host memory); the gradient arrays are null when scoring only.
+struct HostOut {
+  double *log10;
+  uint8_t *flags;
+  float *gb, *gi, *gd;
+  double *gg;
 };
 
 // memcpy split over host threads (large copies only)
@@ -80,20 +93,30 @@ int grow_device(void **p, size_t *cap, size_t need) {
 }
 
 // Wait for a slot's subset and scatter its results to the caller's arrays.
-int drain(Slot &sl, double *out, uint8_t *flags) {
+int drain(Slot &sl, const HostOut &o) {
   if (!sl.busy) return 0;
   if (cudaStreamSynchronize(sl.s) != cudaSuccess) return PHMM_ECUDA;
   const size_t np = (size_t)sl.np;
   const double *r = (const double *)sl.hres;
   const uint8_t *f = (const uint8_t *)(sl.hres + up(8 * np));
   if (sl.contiguous) {
-    par_copy(out + sl.p0, r, 8 * np);
-    std::memcpy(flags + sl.p0, f, np);
+    par_copy(o.log10 + sl.p0, r, 8 * np);
+    std::memcpy(o.flags + sl.p0, f, np);
   } else {
     for (size_t i = 0; i < np; ++i) {
-      out[sl.pairs[i]] = r[i];
-      flags[sl.pairs[i]] = f[i];
+      o.log10[sl.pairs[i]] = r[i];
+      o.flags[sl.pairs[i]] = f[i];
     }
+  }
+  if (o.gb) {
+    const unsigned char *g = sl.hres + sl.grad_off;
+    const size_t gbytes = 4 * (size_t)sl.sm;
+    par_copy(o.gb + sl.b0, g, gbytes);
+    par_copy(o.gi + sl.b0, g + up(gbytes), gbytes);
+    par_copy(o.gd + sl.b0, g + 2 * up(gbytes), gbytes);
+    double gg;
+    std::memcpy(&gg, g + 3 * up(gbytes), 8);
+    *o.gg += gg;
   }
   phmm_plan_destroy(sl.plan);
   sl.plan = nullptr;
@@ -132,16 +155,18 @@ extern "C" void phmm_score_host_release(void) {
   c.device = -1;
 }
 
-extern "C" int phmm_score_host(const phmm_batch *hb, const phmm_options *opt,
-                               int64_t subset_cells, double *out_log10, uint8_t *out_flags) {
-  const phmm::NvtxRange nvtx("phmm_score_host");
-  if (!hb || !out_log10 || !out_flags || subset_cells < 1) return PHMM_EINVAL;
+// The pipeline behind phmm_score_host (dL null) and phmm_grad_host.
+static int host_pipeline(const phmm_batch *hb, const phmm_options *opt, int64_t subset_cells,
+                         const double *dL, const HostOut &ho_) {
+  double *out_log10 = ho_.log10;
+  if (!hb || !out_log10 || !ho_.flags || subset_cells < 1) return PHMM_EINVAL;
+  const bool grad = dL != nullptr;
   const phmm_batch &b = *hb;
   if (b.n_reads < 1 || b.n_haps < 1 || b.n_pairs < 0) return PHMM_EINVAL;
   if (!b.read_bases || !b.base_q || !b.ins_q || !b.del_q || !b.read_off || !b.hap_bases ||
       !b.hap_off || (b.n_pairs > 0 && (!b.pair_read || !b.pair_hap)))
     return PHMM_EINVAL;
-  if (b.n_pairs == 0) return PHMM_OK;
+  if (grad && (!ho_.gb || !ho_.gi || !ho_.gd || !ho_.gg)) return PHMM_EINVAL;
   const int64_t R = b.n_reads, H = b.n_haps, P = b.n_pairs;
   const int64_t *ro = b.read_off, *ho = b.hap_off;
   if (ro[0] != 0 || ho[0] != 0) return PHMM_EINVAL;
@@ -149,6 +174,14 @@ extern "C" int phmm_score_host(const phmm_batch *hb, const phmm_options *opt,
     if (ro[r + 1] <= ro[r]) return PHMM_EINVAL;
   for (int64_t h = 0; h < H; ++h)
     if (ho[h + 1] <= ho[h]) return PHMM_EINVAL;
+  if (grad) {  // reads without pairs keep zero gradients
+    *ho_.gg = 0.0;
+    const size_t sm_all = (size_t)ro[R] * 4;
+    std::memset(ho_.gb, 0, sm_all);
+    std::memset(ho_.gi, 0, sm_all);
+    std::memset(ho_.gd, 0, sm_all);
+  }
+  if (P == 0) return PHMM_OK;
   // pairs grouped by read: already so when pair_read is non-decreasing (all-vs-all batches
   // list a read's pairs together), else by a counting sort
   std::vector<int64_t> rptr(R + 1, 0), rpairs;
@@ -187,10 +220,24 @@ extern "C" int phmm_score_host(const phmm_batch *hb, const phmm_options *opt,
   std::vector<int64_t> hmark(H, -1);
   std::vector<int32_t> hmap(H, 0);
   int64_t lo = 0, k = 0;
+  // Subset sizes ramp up over the first subsets (1/8, 1/4, 1/2 of subset_cells) and halve
+  // over the last ones (down to 1/8), so the copies and host packing that nothing overlaps,
+  // the first subset's inputs and the last one's results, stay small.
+  int64_t left = 0;
+  for (int64_t r = 0; r < R; ++r) {
+    const int64_t m = ro[r + 1] - ro[r];
+    for (int64_t i = rptr[r]; i < rptr[r + 1]; ++i) {
+      const int32_t h = b.pair_hap[pair_at(i)];
+      left += m * (ho[h + 1] - ho[h]);
+    }
+  }
   while (rc == 0 && lo < R) {
-    // the next subset: whole reads up to about subset_cells cells
+    // the next subset: whole reads up to about `target` cells
+    int64_t target = k < 3 ? subset_cells >> (3 - k) : subset_cells;
+    if (left < 2 * target) target = std::max(left / 2, subset_cells / 8);
+    target = std::max<int64_t>(target, 1);
     int64_t hi = lo, cells = 0;
-    while (hi < R && (hi == lo || cells < subset_cells)) {
+    while (hi < R && (hi == lo || cells < target)) {
       const int64_t m = ro[hi + 1] - ro[hi];
       for (int64_t i = rptr[hi]; i < rptr[hi + 1]; ++i) {
         const int32_t h = b.pair_hap[pair_at(i)];
@@ -198,13 +245,18 @@ extern "C" int phmm_score_host(const phmm_batch *hb, const phmm_options *opt,
       }
       ++hi;
     }
+    left -= cells;
     Slot &sl = slot[k & 1];
-    if ((rc = drain(sl, out_log10, out_flags))) break;
+    if ((rc = drain(sl, ho_))) break;
     // the subset's pairs and haplotypes.  Fast path: the pairs are one contiguous range and
     // the haplotypes they use fill most of one contiguous range [hmin, hmax], which is then
     // copied whole and renumbered by offset; otherwise haplotypes are renumbered in
     // first-use order and gathered one by one.
     const int64_t p0 = rptr[lo], np = rptr[hi] - rptr[lo], nr = hi - lo;
+    if (np == 0) {  // reads without pairs: nothing to score (their gradients stay zero)
+      lo = hi;
+      continue;
+    }
     sl.contiguous = sorted;
     sl.p0 = p0;
     if (sorted) sl.pairs.clear();
@@ -235,17 +287,22 @@ extern "C" int phmm_score_host(const phmm_batch *hb, const phmm_options *opt,
     }
     const int64_t nh = hrange ? (int64_t)(hmax - hmin + 1) : (int64_t)haps.size();
     const int64_t sm = ro[hi] - ro[lo];
-    // packed layout: bases, 3 quals, read offsets, haplotype bases and offsets, pair ids
-    size_t off[9], tot = 0;
-    const size_t sz[9] = {(size_t)sm, (size_t)sm * qe, (size_t)sm * qe, (size_t)sm * qe,
-                          (size_t)(nr + 1) * 8, (size_t)sn, (size_t)(nh + 1) * 8,
-                          (size_t)np * 4, (size_t)np * 4};
-    for (int i = 0; i < 9; ++i) {
+    // packed layout: bases, 3 quals, read offsets, haplotype bases and offsets, pair ids,
+    // and (gradient mode) the pairs' dL
+    size_t off[10], tot = 0;
+    const size_t sz[10] = {(size_t)sm, (size_t)sm * qe, (size_t)sm * qe, (size_t)sm * qe,
+                           (size_t)(nr + 1) * 8, (size_t)sn, (size_t)(nh + 1) * 8,
+                           (size_t)np * 4, (size_t)np * 4, grad ? (size_t)np * 8 : 0};
+    for (int i = 0; i < 10; ++i) {
       off[i] = tot;
       tot += up(sz[i]);
     }
     sl.res_off = tot;
-    const size_t res = up(8 * (size_t)np) + up((size_t)np);
+    sl.b0 = ro[lo];
+    sl.sm = sm;
+    // results: log10 L, flags, and (gradient mode) the three per-base gradients and d/dgcp
+    sl.grad_off = up(8 * (size_t)np) + up((size_t)np);
+    const size_t res = sl.grad_off + (grad ? 3 * up(4 * (size_t)sm) + up(8) : 0);
     if ((rc = grow_pinned(&sl.stage, &sl.stage_cap, tot))) break;
     if ((rc = grow_pinned(&sl.hres, &sl.hres_cap, res))) break;
     if ((rc = grow_device((void **)&sl.dev, &sl.dev_cap, tot + res))) break;
@@ -270,10 +327,15 @@ extern "C" int phmm_score_host(const phmm_batch *hb, const phmm_options *opt,
       }
     }
     int32_t *spr = (int32_t *)(st + off[7]), *sph = (int32_t *)(st + off[8]);
+    double *sdl = (double *)(st + off[9]);
     for (int64_t i = 0; i < np; ++i) {
       const int64_t p = pair_at(p0 + i);
       spr[i] = (int32_t)(b.pair_read[p] - lo);
       sph[i] = hrange ? b.pair_hap[p] - hmin : hmap[b.pair_hap[p]];
+    }
+    if (grad) {
+      if (sorted) par_copy(sdl, dL + p0, 8 * (size_t)np);
+      else for (int64_t i = 0; i < np; ++i) sdl[i] = dL[pair_at(p0 + i)];
     }
     if (cudaMemcpyAsync(sl.dev, st, tot, cudaMemcpyHostToDevice, sl.s) != cudaSuccess) {
       rc = PHMM_ECUDA;
@@ -298,7 +360,18 @@ extern "C" int phmm_score_host(const phmm_batch *hb, const phmm_options *opt,
     if ((rc = grow_device(&sl.ws, &sl.ws_cap, wsb + 256))) break;
     double *dout = (double *)(sl.dev + sl.res_off);
     uint8_t *dfl = (uint8_t *)(sl.dev + sl.res_off + up(8 * (size_t)np));
-    if ((rc = phmm_forward(sl.plan, sl.ws, wsb, dout, dfl, sl.s))) break;
+    if (grad) {
+      unsigned char *g = sl.dev + sl.res_off + sl.grad_off;
+      const size_t gbytes = up(4 * (size_t)sm);
+      if ((rc = phmm_forward_partials(sl.plan, sl.ws, wsb, dout, dfl, sl.s))) break;
+      if ((rc = phmm_backward_partials(sl.plan, sl.ws, wsb, (const double *)(sl.dev + off[9]),
+                                       (float *)g, (float *)(g + gbytes),
+                                       (float *)(g + 2 * gbytes), (double *)(g + 3 * gbytes),
+                                       sl.s)))
+        break;
+    } else {
+      if ((rc = phmm_forward(sl.plan, sl.ws, wsb, dout, dfl, sl.s))) break;
+    }
     if (cudaMemcpyAsync(sl.hres, sl.dev + sl.res_off, res, cudaMemcpyDeviceToHost, sl.s) !=
         cudaSuccess) {
       rc = PHMM_ECUDA;
@@ -309,7 +382,7 @@ extern "C" int phmm_score_host(const phmm_batch *hb, const phmm_options *opt,
     ++k;
   }
   for (auto &sl : slot) {
-    const int r2 = rc ? (cudaStreamSynchronize(sl.s), 0) : drain(sl, out_log10, out_flags);
+    const int r2 = rc ? (cudaStreamSynchronize(sl.s), 0) : drain(sl, ho_);
     if (!rc) rc = r2;
     if (sl.plan) phmm_plan_destroy(sl.plan);
     sl.plan = nullptr;
@@ -320,4 +393,21 @@ extern "C" int phmm_score_host(const phmm_batch *hb, const phmm_options *opt,
     cc.device = -1;
   }
   return rc;
+}
+
+extern "C" int phmm_score_host(const phmm_batch *hb, const phmm_options *opt,
+                               int64_t subset_cells, double *out_log10, uint8_t *out_flags) {
+  const phmm::NvtxRange nvtx("phmm_score_host");
+  return host_pipeline(hb, opt, subset_cells, nullptr,
+                       HostOut{out_log10, out_flags, nullptr, nullptr, nullptr, nullptr});
+}
+
+extern "C" int phmm_grad_host(const phmm_batch *hb, const phmm_options *opt,
+                              int64_t subset_cells, const double *dL, double *out_log10,
+                              uint8_t *out_flags, float *d_base_q, float *d_ins_q,
+                              float *d_del_q, double *d_gcp) {
+  const phmm::NvtxRange nvtx("phmm_grad_host");
+  if (!dL) return PHMM_EINVAL;
+  return host_pipeline(hb, opt, subset_cells, dL,
+                       HostOut{out_log10, out_flags, d_base_q, d_ins_q, d_del_q, d_gcp});
 }

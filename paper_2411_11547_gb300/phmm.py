@@ -106,6 +106,9 @@ def lib():
             L.phmm_score_host.argtypes = [ctypes.POINTER(Batch), ctypes.POINTER(Options),
                                           ctypes.c_int64, vp, vp]
             L.phmm_score_host.restype = ctypes.c_int
+            L.phmm_grad_host.argtypes = [ctypes.POINTER(Batch), ctypes.POINTER(Options),
+                                         ctypes.c_int64, vp, vp, vp, vp, vp, vp, vp]
+            L.phmm_grad_host.restype = ctypes.c_int
             L.phmm_score_host_release.argtypes = []
             L.phmm_score_host_release.restype = None
             L.phmm_probe_pipe.argtypes = [ctypes.c_int, ctypes.c_int,
@@ -400,6 +403,32 @@ def score_host(batch, opts: Options | None = None, subset_cells: int = 1 << 33):
     if rc != PHMM_OK:
         raise PhmmError(rc, "phmm_score_host")
     return out, flags
+
+
+def grad_host(batch, dL, opts: Options | None = None, subset_cells: int = 1 << 37, out=None):
+    """phmm_grad_host: log10 L, flags and d(loss)/d(base_q, ins_q, del_q, gcp) (numpy) of a
+    batch held in host memory, given dL = d(loss)/d(log10 L) per pair (host), in pipelined
+    subsets of about `subset_cells` cells.  `out`: optional preallocated
+    (log10 [P] f64, flags [P] u8, dbq, diq, ddq [sum m] f32) arrays to write into."""
+    keep = []
+    b = host_batch_struct(batch, keep)
+    P = b.n_pairs
+    sm = int(np.asarray(batch["read_off"])[-1])
+    if out is None:
+        out = (np.empty(P, dtype=np.float64), np.empty(P, dtype=np.uint8),
+               np.empty(sm, dtype=np.float32), np.empty(sm, dtype=np.float32),
+               np.empty(sm, dtype=np.float32))
+    y, flags, gb, gi, gd = out
+    dL = np.ascontiguousarray(dL, dtype=np.float64)
+    if dL.shape != (P,):
+        raise ValueError("dL must hold one value per pair")
+    gg = ctypes.c_double()
+    rc = lib().phmm_grad_host(ctypes.byref(b), ctypes.byref(opts) if opts is not None else None,
+                              int(subset_cells), dL.ctypes.data, y.ctypes.data, flags.ctypes.data,
+                              gb.ctypes.data, gi.ctypes.data, gd.ctypes.data, ctypes.byref(gg))
+    if rc != PHMM_OK:
+        raise PhmmError(rc, "phmm_grad_host")
+    return y, flags, gb, gi, gd, gg.value
 
 
 def probe_pipe(kind: int, iters: int = 4000):

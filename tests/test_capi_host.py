@@ -127,3 +127,26 @@ def test_score_host_rejects_bad_input_before_touching_the_gpu(lib):
     s2 = phmm.host_batch_struct(bad, keep)
     assert lib.phmm_score_host(ctypes.byref(s2), None, 10, out.ctypes.data,
                                fl.ctypes.data) == phmm.PHMM_EINVAL
+
+
+def test_grad_host_rejects_bad_input_before_touching_the_gpu(lib):
+    import numpy as np
+    from paper_2411_11547_gb300 import phmm, synth
+    b = synth.random_pairs(4, 6, (5, 10), (5, 10))
+    keep = []
+    s = phmm.host_batch_struct(b, keep)
+    sm = int(b["read_off"][-1])
+    out, fl = np.empty(6), np.empty(6, dtype=np.uint8)
+    g = [np.empty(sm, dtype=np.float32) for _ in range(3)]
+    gg = ctypes.c_double()
+    dL = np.ones(6)
+    args = [out.ctypes.data, fl.ctypes.data] + [x.ctypes.data for x in g] + [ctypes.byref(gg)]
+    assert lib.phmm_grad_host(ctypes.byref(s), None, 10, None, *args) == phmm.PHMM_EINVAL
+    no_grad = args[:2] + [None, None, None, ctypes.byref(gg)]
+    assert lib.phmm_grad_host(ctypes.byref(s), None, 10, dL.ctypes.data,
+                              *no_grad) == phmm.PHMM_EINVAL
+    bad = dict(b, pair_hap=b["pair_hap"].copy())
+    bad["pair_hap"][2] = 99
+    s2 = phmm.host_batch_struct(bad, keep)
+    assert lib.phmm_grad_host(ctypes.byref(s2), None, 10, dL.ctypes.data,
+                              *args) == phmm.PHMM_EINVAL

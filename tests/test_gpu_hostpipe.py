@@ -61,3 +61,67 @@ def test_host_pipeline_buffers_are_reused_then_released(phmm):
     for x in (r2, r3):
         assert np.array_equal(r1[0], x[0]) and np.array_equal(r1[1], x[1])
     phmm.lib().phmm_score_host_release()
+
+
+def fused_device(ph, b, dL):
+    """The fused step on the whole batch on the device (reference for phmm_grad_host)."""
+    import torch
+    plan = ph.Plan(ph.DeviceBatch(b))
+    y, fl = plan.forward_partials()
+    gb, gi, gd, gg = plan.backward_partials(torch.as_tensor(dL, device="cuda"))
+    return (y.cpu().numpy(), fl.cpu().numpy(), gb.cpu().numpy(), gi.cpu().numpy(),
+            gd.cpu().numpy(), float(gg.cpu().numpy()[0]))
+
+
+@pytest.mark.parametrize("subset_cells", [1, 300_000, 1 << 40])
+def test_grad_host_matches_oracle_and_whole_batch(phmm, subset_cells):
+    """Per subset the same groups compute each pair's partials and each read's pairs are
+    summed in the same order, so log10 L, flags and the per-read gradients equal the
+    whole-batch fused step bit for bit; d/dgcp is summed over subsets (rounding only)."""
+    from test_gpu_backward import grad_close
+    b = synth.c1_batched(regions=4)
+    b = dict(b, base_q=b["base_q"].astype(np.float32), ins_q=b["ins_q"].astype(np.float32),
+             del_q=b["del_q"].astype(np.float32))
+    dL = np.random.default_rng(8).uniform(-1, 1, len(b["pair_read"]))
+    y, fl, gb, gi, gd, gg = phmm.grad_host(b, dL, subset_cells=subset_cells)
+    ref = fused_device(phmm, b, dL)
+    for got, want in zip((y, fl, gb, gi, gd), ref[:5]):
+        assert np.array_equal(got, want)
+    assert abs(gg - ref[5]) <= 1e-12 * max(1.0, abs(ref[5]))
+    if subset_cells == 300_000:
+        wy, wb, wi, wd, wg = oracle.backward_batch(b, dL)
+        assert np.all(np.abs(y - wy) <= 1e-3)
+        grad_close(gb, wb, "d/dbq")
+        grad_close(gi, wi, "d/diq")
+        grad_close(gd, wd, "d/ddq")
+        assert abs(gg - wg) <= 1e-3 * abs(wg) + 1e-9
+
+
+def test_grad_host_unsorted_pairs_and_reads_without_pairs(phmm):
+    # pairs in random order; the last read has no pair (its gradients are 0); u8 quals
+    b = synth.random_pairs(23, 60, (5, 200), (5, 300), related=0.5)
+    perm = np.random.default_rng(4).permutation(len(b["pair_read"]))
+    keep = perm[perm != np.nonzero(b["pair_read"] == b["pair_read"].max())[0][0]]
+    b = dict(b, pair_read=b["pair_read"][keep].copy(), pair_hap=b["pair_hap"][keep].copy())
+    dL = np.linspace(-2, 2, len(b["pair_read"]))
+    y, fl, gb, gi, gd, gg = phmm.grad_host(b, dL, subset_cells=40_000)
+    ref = fused_device(phmm, b, dL)
+    for got, want in zip((y, fl, gb, gi, gd), ref[:5]):
+        assert np.array_equal(got, want)
+    last = slice(int(b["read_off"][-2]), int(b["read_off"][-1]))
+    assert not gb[last].any() and not gi[last].any() and not gd[last].any()
+    # a subset made only of reads without pairs is skipped (scoring path too)
+    for sc in (1, 40_000):
+        got, flags = phmm.score_host(b, subset_cells=sc)
+        dev, dflags = phmm.forward(b)
+        assert np.array_equal(got, dev.cpu().numpy())
+        assert np.array_equal(flags, dflags.cpu().numpy())
+    phmm.lib().phmm_score_host_release()
+
+
+def test_grad_host_rejects_long_reads_and_missing_arrays(phmm):
+    b = synth.random_pairs(2, 3, (600, 700), (600, 700))
+    with pytest.raises(phmm.PhmmError) as e:
+        phmm.grad_host(b, np.ones(3))
+    assert e.value.status == phmm.PHMM_ETOOLONG
+    phmm.lib().phmm_score_host_release()
