@@ -536,13 +536,18 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
           H = h;
         }
         // Products are added unless the step's posterior scale is negligible (h < kHmin on a
-        // live lane).  Lanes that are not live add zeros (all forward or all adjoint values
-        // zero), garbage that is discarded (pad lanes) or garbage of a pair that goes to FP64
-        // (h > kHmax): no per-row branch.
+        // live lane): such a lane zeroes its forward values for the step (every product has
+        // one as a factor), so all lanes of the warp run the same code.  Lanes that are not
+        // live add zeros (all forward or all adjoint values zero), garbage that is discarded
+        // (pad lanes) or garbage of a pair that goes to FP64 (h > kHmax): no per-row branch.
         const bool quiet = live && h < kHmin;
+        if (quiet) {
+#pragma unroll
+          for (int k = 0; k < 3 * K; ++k) rec[k] = 0;
+        }
+        const T fSq = quiet ? (T)0 : fS;
         T ub = ubK, Ibl = rI;
-        auto rows = [&](auto prod_tag) {
-          constexpr bool PROD = decltype(prod_tag)::value;
+        {
 #pragma unroll
           for (int r = K - 1; r >= 0; --r) {
             const T apB = r == K - 1 ? apb : ap[r + 1];
@@ -558,7 +563,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
             const T Il = eiB * Ibl;
             const T Dn = uba + eps * as.Db[r];                           // D^(r, j)
             const T un = e[r] * Mb;                                      // u(r, j)
-            if constexpr (PROD) {
+            {
               if (r == K - 1) {
                 gAl += uba * Mv;
                 gDl += Ibl * Mv;
@@ -581,12 +586,8 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
             Ibl = Ib;
           }
           // lane 0's row above: u(0, j+1) times the boundary S = K0 D(0, j)
-          if constexpr (PROD) gS += fabs(ub) * fS;
-        };
-        if (!quiet)
-          rows(std::true_type{});
-        else
-          rows(std::false_type{});
+          gS += fabs(ub) * fSq;
+        }
         as.Itop = Ibl;
         const int sf = b + u2 + 1;  // forward step just reversed
         const bool apply = sf <= fin && (u2 == 0 || sf > fin - ramp_b);
