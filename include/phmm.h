@@ -240,9 +240,7 @@ int phmm_autotune(const phmm_batch *batch, phmm_options *opt, int which, int64_t
  * End-to-end scoring of a batch held in HOST memory (the host workflow of Sec. III-A:
  * partition, transfer, score, transfer back).  Every pointer of *host_batch is host memory
  * (pageable or pinned); out_log10 / out_flags are host arrays of n_pairs.  Pairs are grouped by
- * read and cut into subsets of about `subset_cells` cells (Eq. 5; at least one read each;
- * the first three subsets take 1/8, 1/4 and 1/2 of that, and the last ones halve what is left
- * down to 1/8, so the transfers that cannot overlap any computation stay small).
+ * read and cut into subsets of about `subset_cells` cells (Eq. 5; at least one read each).
  * Each subset is packed into pinned staging memory, copied to the device in one transfer,
  * validated and scored with phmm_plan_create / phmm_forward (options `opt`, NULL = defaults;
  * CUDA graphs are not used), and its results copied back, on one of two streams, so the host
@@ -265,7 +263,9 @@ void phmm_score_host_release(void);
  *   d_base_q, d_ins_q, d_del_q : host float [sum m], as phmm_backward (reads without pairs: 0);
  *   d_gcp                      : host double [1], summed over the subsets in order.
  * A subset holds every pair of its reads, so each read's gradient comes from one subset's
- * FP64 reduction.  The copies of one subset overlap the computation of the previous one.
+ * FP64 reduction.  The first three subsets take 1/8, 1/4 and 1/2 of subset_cells and the last
+ * ones halve what is left (down to 1/8), so the transfers that cannot overlap any computation
+ * stay small.  The copies of one subset overlap the computation of the previous one.
  * Errors: those of phmm_score_host, PHMM_EINVAL for a NULL dL or gradient array,
  * PHMM_ETOOLONG for reads longer than PHMM_MAX_READ_LEN.  Shares phmm_score_host's buffers
  * and lock.

@@ -220,9 +220,11 @@ static int host_pipeline(const phmm_batch *hb, const phmm_options *opt, int64_t 
   std::vector<int64_t> hmark(H, -1);
   std::vector<int32_t> hmap(H, 0);
   int64_t lo = 0, k = 0;
-  // Subset sizes ramp up over the first subsets (1/8, 1/4, 1/2 of subset_cells) and halve
-  // over the last ones (down to 1/8), so the copies and host packing that nothing overlaps,
-  // the first subset's inputs and the last one's results, stay small.
+  // Gradient mode: subset sizes ramp up over the first subsets (1/8, 1/4, 1/2 of
+  // subset_cells) and halve over the last ones (down to 1/8), so the copies and host packing
+  // that nothing overlaps, the first subset's inputs and the last one's results, stay small.
+  // A forward subset is short on the GPU (about 1/20 of a gradient subset's time per cell):
+  // there the extra subsets' fixed costs outweigh that (measured), so its size is fixed.
   int64_t left = 0;
   for (int64_t r = 0; r < R; ++r) {
     const int64_t m = ro[r + 1] - ro[r];
@@ -233,8 +235,11 @@ static int host_pipeline(const phmm_batch *hb, const phmm_options *opt, int64_t 
   }
   while (rc == 0 && lo < R) {
     // the next subset: whole reads up to about `target` cells
-    int64_t target = k < 3 ? subset_cells >> (3 - k) : subset_cells;
-    if (left < 2 * target) target = std::max(left / 2, subset_cells / 8);
+    int64_t target = subset_cells;
+    if (grad) {
+      if (k < 3) target = subset_cells >> (3 - k);
+      if (left < 2 * target) target = std::max(left / 2, subset_cells / 8);
+    }
     target = std::max<int64_t>(target, 1);
     int64_t hi = lo, cells = 0;
     while (hi < R && (hi == lo || cells < target)) {
