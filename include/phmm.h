@@ -103,7 +103,8 @@ typedef struct phmm_options {
   int32_t warps_per_block; /* 1..4 warps per block (0 = 4) */
   int32_t bin_rows[PHMM_MAX_READ_LEN / 4 + 1]; /* optional read-length -> group table */
   int32_t bin_table_valid; /* 1 if bin_rows holds a table */
-  int32_t adjoint_rescue;  /* 1: adjoints out of the FP32 range are redone in FP64; 0: NaN */
+  int32_t adjoint_rescue;  /* 1: adjoints out of the FP32 range are redone in FP64; 0: NaN;
+                              2: every pair's adjoint in FP64 (reference gradients, slower) */
   int32_t bwd_rows[PHMM_MAX_READ_LEN / 4 + 1]; /* optional read-length -> adjoint group table */
   int32_t bwd_table_valid; /* 1 if bwd_rows holds a table */
   int32_t bwd_warps_per_block; /* adjoint launches: 1..4 (0 = warps_per_block) */

@@ -263,6 +263,7 @@ int bwd_sweep_impl(phmm_plan *pl, char *ws, const double *dL, double *out, uint8
       c.nchk = (int32_t)bwd_nchk(L, K, 4, nmax);
       c.slot_elems = slot_elems(L, K, 4, nmax);
       c.rescue = o.adjoint_rescue ? 0 : 1;  // without the FP64 pass, failures write NaN
+      c.all64 = o.adjoint_rescue == 2 ? 1 : 0;
       BwdKernel k = bwd_kernel32(L, K);
       if (!k) return (int)cudaErrorInvalidValue;
       const int block = bwd_block(K, 4, o.bwd_warps_per_block);

@@ -21,6 +21,7 @@ struct BwdArgs {
   int64_t slot_elems;
   int32_t nchk;            // checkpoint capacity per slot
   int32_t rescue;          // 1: this is the FP64 pass (write NaN on failure)
+  int32_t all64;           // FP32 pass: hand every valid pair to the FP64 pass untouched
   int32_t *resc_list[kNumCfg64];  // FP32 pass: pairs handed to the FP64 pass
   int32_t *resc_count;
   int32_t *why;                   // [2]: hand-offs for the scale range / non-finite partials
@@ -246,6 +247,13 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
         m = 0;
         n = 0;
       }
+    }
+    if (a.all64) {  // warp-uniform: every pair of the item goes to the FP64 pass as it is
+      if (valid && !bad && t == 0) {
+        const int bin = bin64_of_m(m);
+        a.resc_list[bin][atomicAdd(&a.resc_count[bin], 1)] = p;
+      }
+      continue;
     }
     const int npad = L * K - m;
     // pad rows: the rows above row 1 (their partials are never used)

@@ -329,6 +329,7 @@ int phmm_plan_create(const phmm_batch *batch, const phmm_options *opt, void *str
   if (b.alpha_mode != 0 && b.alpha_mode != 1) return PHMM_EINVAL;
   if (!(b.gcp > 0.0) || !std::isfinite(b.gcp)) return PHMM_EINVAL;
   if (o.first_line != PHMM_FIRST_PLAIN32 && o.first_line != PHMM_FIRST_EXT32) return PHMM_EINVAL;
+  if (o.adjoint_rescue < 0 || o.adjoint_rescue > 2) return PHMM_EINVAL;
   if (!o.binning && !valid_group(o.lanes, o.rows)) return PHMM_EINVAL;
   (void)cudaGetLastError();  // drop a stale error left by an unrelated call
   if (o.warps_per_block <= 0) o.warps_per_block = 4;

@@ -150,3 +150,19 @@ def test_grad_host_rejects_bad_input_before_touching_the_gpu(lib):
     s2 = phmm.host_batch_struct(bad, keep)
     assert lib.phmm_grad_host(ctypes.byref(s2), None, 10, dL.ctypes.data,
                               *args) == phmm.PHMM_EINVAL
+
+
+def test_plan_create_rejects_bad_options_before_touching_the_gpu(lib):
+    # option checks come before any device work, so host pointers (never read) serve here
+    import numpy as np
+    from paper_2411_11547_gb300 import phmm, synth
+    b = synth.random_pairs(4, 6, (5, 10), (5, 10))
+    keep = []
+    s = phmm.host_batch_struct(b, keep)
+    h = ctypes.c_void_p()
+    for kw in ({"adjoint_rescue": 3}, {"adjoint_rescue": -1}, {"first_line": 7},
+               {"warps_per_block": 8}):
+        o = phmm.options(**kw)
+        assert lib.phmm_plan_create(ctypes.byref(s), ctypes.byref(o), None,
+                                    ctypes.byref(h)) == phmm.PHMM_EINVAL, kw
+        assert not h.value

@@ -251,3 +251,39 @@ def test_c4_adjoint_full_size_sampled_regions(phmm):
     grad_close(fb.cpu().numpy()[idx], wb[idx], "fused d/dbq")
     grad_close(fi.cpu().numpy()[idx], wi[idx], "fused d/diq")
     grad_close(fd.cpu().numpy()[idx], wd[idx], "fused d/ddq")
+
+
+def test_fused_step_empty_batch(phmm):
+    import torch
+    # no pairs: log10 L is empty, every gradient is 0
+    b = synth.random_pairs(2, 3, (5, 10), (5, 10), qual_dtype=np.float32)
+    b = dict(b, pair_read=b["pair_read"][:0], pair_hap=b["pair_hap"][:0])
+    plan = phmm.Plan(phmm.DeviceBatch(b))
+    y, fl = plan.forward_partials()
+    gb, gi, gd, gg = plan.backward_partials(torch.zeros(0, dtype=torch.float64, device="cuda"))
+    assert y.shape == (0,) and fl.shape == (0,)
+    for g in (gb, gi, gd):
+        assert not g.cpu().numpy().any()
+    assert float(gg.cpu()[0]) == 0.0
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_every_pair_in_fp64(phmm, fused):
+    """adjoint_rescue = 2 sends every pair to the FP64 adjoint (32 lanes x 4 / 8 / 16 rows, by
+    read length): the FP64 kernels that otherwise run only on hand-offs, against the oracle;
+    the fused call's log10 L then comes from FP64 too (the rescued-pair bar, 1e-9)."""
+    b = synth.random_pairs(44, 60, (1, 500), (1, 400), related=0.6, qual_dtype=np.float32)
+    rl = np.diff(b["read_off"])[b["pair_read"]]
+    assert (rl <= 128).any() and ((rl > 128) & (rl <= 256)).any() and (rl > 256).any()
+    P = len(b["pair_read"])
+    dy = np.random.default_rng(5).uniform(-1, 1, P)
+    wy, wb, wi, wd, wg = oracle.backward_batch(b, dy)
+    y, gb, gi, gd, gg, plan, fl = run_grad(phmm, b, dy, fused=fused, adjoint_rescue=2)
+    assert plan.rescue_counts()[2] == P
+    if fused:
+        assert np.all(fl == (phmm.FLAG_RESCUED64 | phmm.FLAG_EXTENDED))
+        assert np.all(np.abs(y - wy) <= 1e-9)
+    grad_close(gb, wb, "d/dbq")
+    grad_close(gi, wi, "d/diq")
+    grad_close(gd, wd, "d/ddq")
+    assert abs(gg - wg) <= 1e-6 * abs(wg) + 1e-9, (gg, wg)
