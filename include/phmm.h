@@ -242,7 +242,9 @@ int phmm_autotune(const phmm_batch *batch, phmm_options *opt, int which, int64_t
  * partition, transfer, score, transfer back).  Every pointer of *host_batch is host memory
  * (pageable or pinned); out_log10 / out_flags are host arrays of n_pairs.  Pairs are grouped by
  * read and cut into subsets of about `subset_cells` cells (Eq. 5; at least one read each).
- * Each subset is packed into pinned staging memory, copied to the device in one transfer,
+ * Each subset is packed into pinned staging memory, copied to the device in one transfer
+ * (on a device that reads pageable host memory coherently, e.g. over NVLink-C2C, only its
+ * offsets and pair ids are: the kernels read bases, qualities and haplotypes in place),
  * validated and scored with phmm_plan_create / phmm_forward (options `opt`, NULL = defaults;
  * CUDA graphs are not used), and its results copied back, on one of two streams, so the host
  * packing and copies of one subset overlap the scoring of the previous one.  Returns when

@@ -124,6 +124,22 @@ int drain(Slot &sl, const HostOut &o) {
   return 0;
 }
 
+// 1 if kernels on device `dev` may read pageable host memory in place (coherent host access
+// through the host's page tables, as on Grace-Blackwell over NVLink-C2C).
+bool host_direct(int dev) {
+  static int cached[64] = {};  // 0 unknown, 1 no, 2 yes
+  int &c = cached[dev & 63];
+  if (!c) {
+    int v = 0, w = 0;
+    const bool ok =
+        cudaDeviceGetAttribute(&v, cudaDevAttrPageableMemoryAccess, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&w, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev) ==
+            cudaSuccess;
+    c = ok && v && w ? 2 : 1;
+  }
+  return c == 2;
+}
+
 // Staging and device buffers kept between calls (pinned allocations are slow to make), for
 // the device they were made on; one call at a time uses them.
 struct Cache {
@@ -213,6 +229,12 @@ static int host_pipeline(const phmm_batch *hb, const phmm_options *opt, int64_t 
     cc.device = dev;
   }
   Slot(&slot)[2] = cc.slot;
+  // Forward scoring with coherent host access: the kernels read the subset's bases, qualities
+  // and (contiguous) haplotypes where they lie, and only offsets and pair ids are packed and
+  // copied (host packing bounds this path).  The gradient keeps the copies: its subsets run
+  // long adjoint kernels, and reading in place from kernels that must wait for SMs measured
+  // slower than copy-engine transfers that overlap them.
+  const bool direct = !grad && host_direct(dev);
   int rc = 0;
   for (auto &sl : slot)
     if (!sl.s && cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking) != cudaSuccess)
@@ -295,9 +317,11 @@ static int host_pipeline(const phmm_batch *hb, const phmm_options *opt, int64_t 
     // packed layout: bases, 3 quals, read offsets, haplotype bases and offsets, pair ids,
     // and (gradient mode) the pairs' dL
     size_t off[10], tot = 0;
-    const size_t sz[10] = {(size_t)sm, (size_t)sm * qe, (size_t)sm * qe, (size_t)sm * qe,
-                           (size_t)(nr + 1) * 8, (size_t)sn, (size_t)(nh + 1) * 8,
-                           (size_t)np * 4, (size_t)np * 4, grad ? (size_t)np * 8 : 0};
+    const size_t rb = direct ? 0 : (size_t)sm;           // read bases / quals staged
+    const size_t hb = direct && hrange ? 0 : (size_t)sn;   // haplotype bases staged
+    const size_t sz[10] = {rb, rb * qe, rb * qe, rb * qe, (size_t)(nr + 1) * 8, hb,
+                           (size_t)(nh + 1) * 8, (size_t)np * 4, (size_t)np * 4,
+                           grad ? (size_t)np * 8 : 0};
     for (int i = 0; i < 10; ++i) {
       off[i] = tot;
       tot += up(sz[i]);
@@ -312,16 +336,18 @@ static int host_pipeline(const phmm_batch *hb, const phmm_options *opt, int64_t 
     if ((rc = grow_pinned(&sl.hres, &sl.hres_cap, res))) break;
     if ((rc = grow_device((void **)&sl.dev, &sl.dev_cap, tot + res))) break;
     unsigned char *st = sl.stage;
-    par_copy(st + off[0], b.read_bases + ro[lo], sm);
-    par_copy(st + off[1], (const unsigned char *)b.base_q + ro[lo] * qe, sm * qe);
-    par_copy(st + off[2], (const unsigned char *)b.ins_q + ro[lo] * qe, sm * qe);
-    par_copy(st + off[3], (const unsigned char *)b.del_q + ro[lo] * qe, sm * qe);
+    if (!direct) {
+      par_copy(st + off[0], b.read_bases + ro[lo], sm);
+      par_copy(st + off[1], (const unsigned char *)b.base_q + ro[lo] * qe, sm * qe);
+      par_copy(st + off[2], (const unsigned char *)b.ins_q + ro[lo] * qe, sm * qe);
+      par_copy(st + off[3], (const unsigned char *)b.del_q + ro[lo] * qe, sm * qe);
+    }
     int64_t *sro = (int64_t *)(st + off[4]);
     for (int64_t r = 0; r <= nr; ++r) sro[r] = ro[lo + r] - ro[lo];
     int64_t *sho = (int64_t *)(st + off[6]);
     sho[0] = 0;
     if (hrange) {
-      par_copy(st + off[5], b.hap_bases + ho[hmin], sn);
+      if (!direct) par_copy(st + off[5], b.hap_bases + ho[hmin], sn);
       for (int64_t i = 0; i <= nh; ++i) sho[i] = ho[hmin + i] - ho[hmin];
     } else {
       for (int64_t i = 0; i < nh; ++i) {
@@ -350,12 +376,19 @@ static int host_pipeline(const phmm_batch *hb, const phmm_options *opt, int64_t 
     d.n_reads = nr;
     d.n_haps = nh;
     d.n_pairs = np;
-    d.read_bases = sl.dev + off[0];
-    d.base_q = sl.dev + off[1];
-    d.ins_q = sl.dev + off[2];
-    d.del_q = sl.dev + off[3];
+    if (direct) {
+      d.read_bases = b.read_bases + ro[lo];
+      d.base_q = (const unsigned char *)b.base_q + ro[lo] * qe;
+      d.ins_q = (const unsigned char *)b.ins_q + ro[lo] * qe;
+      d.del_q = (const unsigned char *)b.del_q + ro[lo] * qe;
+    } else {
+      d.read_bases = sl.dev + off[0];
+      d.base_q = sl.dev + off[1];
+      d.ins_q = sl.dev + off[2];
+      d.del_q = sl.dev + off[3];
+    }
     d.read_off = (const int64_t *)(sl.dev + off[4]);
-    d.hap_bases = sl.dev + off[5];
+    d.hap_bases = direct && hrange ? b.hap_bases + ho[hmin] : sl.dev + off[5];
     d.hap_off = (const int64_t *)(sl.dev + off[6]);
     d.pair_read = (const int32_t *)(sl.dev + off[7]);
     d.pair_hap = (const int32_t *)(sl.dev + off[8]);
