@@ -248,7 +248,7 @@ static int host_pipeline(const phmm_batch *hb, const phmm_options *opt, int64_t 
   // A forward subset is short on the GPU (about 1/20 of a gradient subset's time per cell):
   // there the extra subsets' fixed costs outweigh that (measured), so its size is fixed.
   int64_t left = 0;
-  for (int64_t r = 0; r < R; ++r) {
+  for (int64_t r = 0; grad && r < R; ++r) {
     const int64_t m = ro[r + 1] - ro[r];
     for (int64_t i = rptr[r]; i < rptr[r + 1]; ++i) {
       const int32_t h = b.pair_hap[pair_at(i)];
@@ -264,11 +264,14 @@ static int host_pipeline(const phmm_batch *hb, const phmm_options *opt, int64_t 
     }
     target = std::max<int64_t>(target, 1);
     int64_t hi = lo, cells = 0;
+    int32_t hmin = INT32_MAX, hmax = -1;  // the haplotypes the subset's pairs use
     while (hi < R && (hi == lo || cells < target)) {
       const int64_t m = ro[hi + 1] - ro[hi];
       for (int64_t i = rptr[hi]; i < rptr[hi + 1]; ++i) {
         const int32_t h = b.pair_hap[pair_at(i)];
         cells += m * (ho[h + 1] - ho[h]);
+        hmin = std::min(hmin, h);
+        hmax = std::max(hmax, h);
       }
       ++hi;
     }
@@ -289,12 +292,6 @@ static int host_pipeline(const phmm_batch *hb, const phmm_options *opt, int64_t 
     if (sorted) sl.pairs.clear();
     else sl.pairs.assign(rpairs.begin() + p0, rpairs.begin() + rptr[hi]);
     sl.np = np;
-    int32_t hmin = INT32_MAX, hmax = -1;
-    for (int64_t i = 0; i < np; ++i) {
-      const int32_t h = b.pair_hap[pair_at(p0 + i)];
-      hmin = std::min(hmin, h);
-      hmax = std::max(hmax, h);
-    }
     std::vector<int32_t> haps;
     int64_t sn = 0;
     bool hrange = false;
