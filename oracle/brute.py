@@ -24,19 +24,24 @@ def _match(r: str, h: str) -> bool:
     return r == h or r == "N" or h == "N"
 
 
-def likelihood(read: str, hap: str, Q, delta, zeta, eps) -> Fraction:
+def likelihood(read: str, hap: str, Q, delta, zeta, eps, alpha=None) -> Fraction:
     """Exact L = sum over paths of the product of transition and emission weights.
 
     Q, delta, zeta: per read position (length m) probabilities (Fraction or anything
     Fraction() accepts exactly, e.g. floats); eps: gap continuation probability.
-    alpha_i = 1 - (delta_i + zeta_i), beta = 1 - eps.
+    alpha_i = 1 - (delta_i + zeta_i) unless ``alpha`` gives the M -> M probability of every
+    read position explicitly (e.g. the alternative 1 - 10^(-(iq_i + dq_i)/10)); beta = 1 - eps.
     """
     m, n = len(read), len(hap)
     Q = [Fraction(x) for x in Q]
     de = [Fraction(x) for x in delta]
     ze = [Fraction(x) for x in zeta]
     ep = Fraction(eps)
-    al = [1 - (de[i] + ze[i]) for i in range(m)]
+    if alpha is None:
+        al = [1 - (de[i] + ze[i]) for i in range(m)]
+    else:
+        al = [Fraction(x) for x in alpha]
+        assert len(al) == m
     be = 1 - ep
 
     def lam(i, j):  # 1-based

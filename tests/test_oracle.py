@@ -242,18 +242,56 @@ def test_mismatch_monotonicity(seed):
         prev = cur
 
 
-def test_alpha_mode_alternative():
-    # alpha_mode 1 uses alpha = 1 - 10^(-(iq+dq)/10); check against enumeration with that alpha
-    rng = np.random.default_rng(5)
-    read, hap = rand_seq(rng, 3), rand_seq(rng, 4)
-    bq, iq, dq = [20.0, 30.0, 12.0], [15.0, 20.0, 25.0], [18.0, 22.0, 9.0]
-    # brute force with alpha folded in: enumerate with delta/zeta but alpha overridden
-    got0 = oracle.forward_pair(read, bq, iq, dq, hap, gcp=10, alpha_mode=0)
-    got1 = oracle.forward_pair(read, bq, iq, dq, hap, gcp=10, alpha_mode=1)
-    a0 = [1 - (P(i) + P(d)) for i, d in zip(iq, dq)]
-    a1 = [1 - P(i + d) for i, d in zip(iq, dq)]
-    assert all(x > y for x, y in zip(a1, a0))
-    assert got1 > got0  # larger M->M probability on every row, all else equal
+@pytest.mark.parametrize("seed", range(6))
+def test_alpha_mode_1_2x3_closed_form(seed):
+    # The hand-derived 2x3 closed form of test_2x3_closed_form with the alternative
+    # M -> M probability alpha_i = 1 - 10^(-(iq_i + dq_i)/10) (alpha_mode 1):
+    # L = (b/3)[l11 l22 a2 + l23 (l12 a2 + b z1 l11) + d2 (l11 + l12 + l13)], a2 replaced.
+    rng = np.random.default_rng(400 + seed)
+    read, hap = rand_seq(rng, 2), rand_seq(rng, 3)
+    bq = rng.integers(5, 41, size=2).astype(float)
+    iq = rng.integers(3, 20, size=2).astype(float)   # low gap quals: the two alphas differ
+    dq = rng.integers(3, 20, size=2).astype(float)   # by ~(delta + zeta) / ln 10 per row
+    gcp = float(rng.uniform(5, 20))
+    Q, d, z = P(bq), P(iq), P(dq)
+    a1 = 1 - 10.0 ** (-(iq + dq) / 10.0)
+    b = 1 - P(gcp)
+
+    def lam(i, j):
+        return (1 - Q[i - 1]) if read[i - 1] == hap[j - 1] else Q[i - 1] / 3
+
+    L1 = (b / 3) * (lam(1, 1) * lam(2, 2) * a1[1]
+                    + lam(2, 3) * (lam(1, 2) * a1[1] + b * z[0] * lam(1, 1))
+                    + d[1] * (lam(1, 1) + lam(1, 2) + lam(1, 3)))
+    got = oracle.forward_pair(read, bq, iq, dq, hap, gcp=gcp, alpha_mode=1)
+    assert got == pytest.approx(math.log10(L1), abs=1e-13)
+    # the default reading gives a different value on the same pair (the pin separates them)
+    got0 = oracle.forward_pair(read, bq, iq, dq, hap, gcp=gcp, alpha_mode=0)
+    assert abs(got0 - got) > 1e-9
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_alpha_mode_1_brute_force(seed):
+    # alpha_mode 1 against exact path enumeration with alpha_i = 1 - 10^(-(iq_i+dq_i)/10)
+    # passed to the enumerator explicitly (everything else as in test_brute_force_tiny)
+    rng = np.random.default_rng(9100 + seed)
+    m = int(rng.integers(1, 5))
+    n = int(rng.integers(1, 6))
+    alph = "ACGTN" if seed % 3 == 0 else "ACGT"
+    read, hap = rand_seq(rng, m, alph), rand_seq(rng, n, alph)
+    bq = rng.integers(0, 41, size=m).astype(float)
+    iq = rng.integers(2, 30, size=m).astype(float)
+    dq = rng.integers(2, 30, size=m).astype(float)
+    gcp = float(rng.integers(1, 40))
+    alpha = [Fraction(1.0 - 10.0 ** (-(i + d) / 10.0)) for i, d in zip(iq, dq)]
+    exact = brute.likelihood(read, hap, [Fraction(P(q)) for q in bq],
+                             [Fraction(P(q)) for q in iq], [Fraction(P(q)) for q in dq],
+                             Fraction(P(gcp)), alpha=alpha)
+    got = oracle.forward_pair(read, bq, iq, dq, hap, gcp=gcp, alpha_mode=1)
+    if exact == 0:
+        assert got == -math.inf
+    else:
+        assert got == pytest.approx(math.log10(exact), abs=1e-12)
 
 
 def test_invalid_inputs_give_nan():
