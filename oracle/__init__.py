@@ -42,6 +42,7 @@ class _Batch(ctypes.Structure):
         ("dq", ctypes.c_void_p), ("read_off", ctypes.c_void_p), ("hap_bases", ctypes.c_void_p),
         ("hap_off", ctypes.c_void_p), ("pair_read", ctypes.c_void_p),
         ("pair_hap", ctypes.c_void_p), ("gcp", ctypes.c_double), ("alpha_mode", ctypes.c_int32),
+        ("gq", ctypes.c_void_p),
     ]
 
 
@@ -54,16 +55,17 @@ def lib():
             L.oracle_forward_pair.restype = ctypes.c_double
             L.oracle_forward_pair.argtypes = [ctypes.c_int, ctypes.c_char_p, dp, dp, dp,
                                               ctypes.c_int, ctypes.c_char_p, ctypes.c_double,
-                                              ctypes.c_int]
+                                              ctypes.c_int, dp]
             L.oracle_backward_pair.restype = ctypes.c_double
             L.oracle_backward_pair.argtypes = [ctypes.c_int, ctypes.c_char_p, dp, dp, dp,
                                                ctypes.c_int, ctypes.c_char_p, ctypes.c_double,
-                                               ctypes.c_int, ctypes.c_double, dp, dp, dp, dp]
+                                               ctypes.c_int, dp, ctypes.c_double, dp, dp, dp, dp,
+                                               dp]
             L.oracle_forward_batch.restype = ctypes.c_int
             L.oracle_forward_batch.argtypes = [ctypes.POINTER(_Batch), dp, ctypes.c_int]
             L.oracle_backward_batch.restype = ctypes.c_int
             L.oracle_backward_batch.argtypes = [ctypes.POINTER(_Batch), dp, dp, dp, dp, dp, dp,
-                                                ctypes.c_int]
+                                                dp, ctypes.c_int]
             _lib = L
     return _lib
 
@@ -82,23 +84,36 @@ def _bytes(s) -> bytes:
     return bytes(np.asarray(s, dtype=np.uint8).tobytes())
 
 
-def forward_pair(read, bq, iq, dq, hap, gcp=10.0, alpha_mode=0) -> float:
-    """log10 P(read | hap) for one pair; quals are Phred values (any real dtype)."""
+def _gq_ptr(gcp_q, m):
+    if gcp_q is None:
+        return None, None
+    g = _f64(gcp_q)
+    assert g.shape == (m,)
+    return g, _dp(g)
+
+
+def forward_pair(read, bq, iq, dq, hap, gcp=10.0, alpha_mode=0, gcp_q=None) -> float:
+    """log10 P(read | hap) for one pair; quals are Phred values (any real dtype).  gcp_q: an
+    optional per-base gap-continuation track (Phred, length m) used instead of gcp."""
     r, h = _bytes(read), _bytes(hap)
     b, i, d = _f64(bq), _f64(iq), _f64(dq)
+    g, gp = _gq_ptr(gcp_q, len(r))
     return lib().oracle_forward_pair(len(r), r, _dp(b), _dp(i), _dp(d), len(h), h, float(gcp),
-                                     int(alpha_mode))
+                                     int(alpha_mode), gp)
 
 
-def backward_pair(read, bq, iq, dq, hap, gcp=10.0, alpha_mode=0, dy=1.0):
-    """(log10 L, d/dbq[m], d/diq[m], d/ddq[m], d/dgcp) of dy * log10 L for one pair."""
+def backward_pair(read, bq, iq, dq, hap, gcp=10.0, alpha_mode=0, dy=1.0, gcp_q=None):
+    """(log10 L, d/dbq[m], d/diq[m], d/ddq[m], d/dgcp) of dy * log10 L for one pair.  With a
+    per-base track gcp_q the last value is d/dgcp_q[m] (per position)."""
     r, h = _bytes(read), _bytes(hap)
     b, i, d = _f64(bq), _f64(iq), _f64(dq)
     m = len(r)
-    gb, gi, gd, gg = np.zeros(m), np.zeros(m), np.zeros(m), np.zeros(1)
+    g, gp = _gq_ptr(gcp_q, m)
+    gb, gi, gd, gq, gg = np.zeros(m), np.zeros(m), np.zeros(m), np.zeros(m), np.zeros(1)
     y = lib().oracle_backward_pair(m, r, _dp(b), _dp(i), _dp(d), len(h), h, float(gcp),
-                                   int(alpha_mode), float(dy), _dp(gb), _dp(gi), _dp(gd), _dp(gg))
-    return y, gb, gi, gd, float(gg[0])
+                                   int(alpha_mode), gp, float(dy), _dp(gb), _dp(gi), _dp(gd),
+                                   _dp(gq), _dp(gg))
+    return y, gb, gi, gd, (gq if gcp_q is not None else float(gg[0]))
 
 
 def _mk_batch(batch, keep):
@@ -122,6 +137,11 @@ def _mk_batch(batch, keep):
         setattr(b, k, a[k].ctypes.data)
     b.gcp = float(batch["gcp"])
     b.alpha_mode = int(batch.get("alpha_mode", 0))
+    if batch.get("gcp_q") is not None:
+        a["gq"] = _f64(batch["gcp_q"])
+        b.gq = a["gq"].ctypes.data
+    else:
+        b.gq = None
     return b
 
 
@@ -139,16 +159,19 @@ def forward_batch(batch, nthreads=None) -> np.ndarray:
 
 
 def backward_batch(batch, dy, nthreads=None):
-    """(log10 L[P], d/dbq[sum m], d/diq[sum m], d/ddq[sum m], d/dgcp) of sum_p dy_p log10 L_p."""
+    """(log10 L[P], d/dbq[sum m], d/diq[sum m], d/ddq[sum m], d/dgcp) of sum_p dy_p log10 L_p.
+    For a batch with a per-base gap-continuation track ("gcp_q", [sum m]) the last value is
+    d/dgcp_q [sum m] instead of the scalar d/dgcp."""
     keep = []
     b = _mk_batch(batch, keep)
     dyv = _f64(dy)
     assert dyv.shape == (b.n_pairs,)
     out = np.empty(b.n_pairs)
     tot = int(keep[0]["read_off"][-1])
-    gb, gi, gd, gg = np.zeros(tot), np.zeros(tot), np.zeros(tot), np.zeros(1)
+    gb, gi, gd, gq, gg = (np.zeros(tot), np.zeros(tot), np.zeros(tot), np.zeros(tot),
+                          np.zeros(1))
     rc = lib().oracle_backward_batch(ctypes.byref(b), _dp(dyv), _dp(out), _dp(gb), _dp(gi),
-                                     _dp(gd), _dp(gg), int(nthreads or default_threads()))
+                                     _dp(gd), _dp(gq), _dp(gg), int(nthreads or default_threads()))
     if rc != 0:
         raise MemoryError("oracle_backward_batch failed")
-    return out, gb, gi, gd, float(gg[0])
+    return out, gb, gi, gd, (gq if batch.get("gcp_q") is not None else float(gg[0]))

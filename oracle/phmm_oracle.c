@@ -10,6 +10,8 @@
  *   Eq. 1  M(i,j) = lambda(i,j) * ( alpha_i M(i-1,j-1) + beta (I(i-1,j-1) + D(i-1,j-1)) )
  *   Eq. 2  I(i,j) = delta_i M(i-1,j) + eps I(i-1,j)
  *   Eq. 3  D(i,j) = zeta_i  M(i,j-1) + eps D(i,j-1)
+ *   (with a per-base gap-continuation track, eps and beta become eps_i and beta_i of the row
+ *   being computed, like alpha_i, delta_i and zeta_i)
  *   init   M(i,0)=I(i,0)=D(i,0)=0 (i>=1); M(0,j)=I(0,j)=0, D(0,j)=1/n (0<=j<=n)
  *   Eq. 4  lambda(i,j) = 1-Q_i if r_i == h_j else Q_i/3
  *   result L = sum_{j=1..n} M(m,j) + I(m,j);  reported as log10 L.
@@ -17,7 +19,8 @@
  * Readings of points the paper leaves open (each one is listed in the design notes):
  *   - transitions (Sec. III-A only says quality scores and gap probabilities are inputs):
  *       Q_i = 10^(-bq_i/10), delta_i = 10^(-iq_i/10), zeta_i = 10^(-dq_i/10),
- *       eps = 10^(-gcp/10), beta = 1 - eps,
+ *       eps = 10^(-gcp/10), beta = 1 - eps  (per-base track: eps_i = 10^(-gcp_i/10),
+ *       beta_i = 1 - eps_i, every transition of row i taken from read position i),
  *       alpha_i = 1 - (delta_i + zeta_i)            (alpha_mode 0, default)
  *       alpha_i = 1 - 10^(-(iq_i + dq_i)/10)        (alpha_mode 1, alternative)
  *   - D(0,0) = 1/n (the init line gives D(0,j)=1/n for every j including 0);
@@ -68,23 +71,26 @@ typedef struct {
   const double *bq, *iq, *dq;
   double gcp;
   int alpha_mode;
+  const double *gq; /* per-base gap-continuation Phred values [m], or NULL: gcp everywhere */
 } or_pair;
 
-/* Per-row transition parameters of one read. */
+/* Per-row transition parameters of one read (index i = 1..m). */
 typedef struct {
-  double *Q, *alpha, *delta, *zeta;
-  double eps, beta;
+  double *Q, *alpha, *delta, *zeta, *eps, *beta;
 } or_params;
 
 static int params_init(const or_pair *p, or_params *t) {
-  t->Q = (double *)malloc(sizeof(double) * 4 * (size_t)(p->m + 1));
+  t->Q = (double *)malloc(sizeof(double) * 6 * (size_t)(p->m + 1));
   if (!t->Q) return OR_ENOMEM;
   t->alpha = t->Q + (p->m + 1);
   t->delta = t->alpha + (p->m + 1);
   t->zeta = t->delta + (p->m + 1);
-  t->eps = phred(p->gcp);
-  t->beta = 1.0 - t->eps;
+  t->eps = t->zeta + (p->m + 1);
+  t->beta = t->eps + (p->m + 1);
+  t->eps[0] = t->beta[0] = 0.0;
   for (int i = 1; i <= p->m; ++i) {
+    t->eps[i] = phred(p->gq ? p->gq[i - 1] : p->gcp);
+    t->beta[i] = 1.0 - t->eps[i];
     t->Q[i] = phred(p->bq[i - 1]);
     t->delta[i] = phred(p->iq[i - 1]);
     t->zeta[i] = phred(p->dq[i - 1]);
@@ -152,9 +158,9 @@ static double forward_rows(const or_pair *p, const or_params *t, double *SM, dou
     cM[0] = cI[0] = cD[0] = 0.0;
     for (int j = 1; j <= n; ++j) {
       double lam = lambda_of(p, t, i, j);
-      cM[j] = lam * (t->alpha[i] * pM[j - 1] + t->beta * (pI[j - 1] + pD[j - 1]));
-      cI[j] = t->delta[i] * pM[j] + t->eps * pI[j];
-      cD[j] = t->zeta[i] * cM[j - 1] + t->eps * cD[j - 1];
+      cM[j] = lam * (t->alpha[i] * pM[j - 1] + t->beta[i] * (pI[j - 1] + pD[j - 1]));
+      cI[j] = t->delta[i] * pM[j] + t->eps[i] * pI[j];
+      cD[j] = t->zeta[i] * cM[j - 1] + t->eps[i] * cD[j - 1];
     }
     int ei = renorm_row(cM, cI, cD, n);
     if (e) e[i] = ei;
@@ -183,15 +189,17 @@ static int check_pair(const or_pair *p) {
     if (isnan(p->bq[i]) || isnan(p->iq[i]) || isnan(p->dq[i])) return OR_EINVAL;
     if (p->bq[i] < 0 || p->iq[i] < 0 || p->dq[i] < 0) return OR_EINVAL;
     if (p->alpha_mode == 0 && phred(p->iq[i]) + phred(p->dq[i]) > 1.0) return OR_EINVAL;
+    if (p->gq && !(p->gq[i] > 0.0)) return OR_EINVAL;
   }
   return OR_OK;
 }
 
-/* log10 P(R | H) for one pair.  Returns NAN for invalid input. */
+/* log10 P(R | H) for one pair.  gq: per-base gap-continuation Phred values [m] or NULL (gcp
+ * everywhere).  Returns NAN for invalid input. */
 double oracle_forward_pair(int m, const uint8_t *r, const double *bq, const double *iq,
                            const double *dq, int n, const uint8_t *h, double gcp,
-                           int alpha_mode) {
-  or_pair p = {m, n, r, h, bq, iq, dq, gcp, alpha_mode};
+                           int alpha_mode, const double *gq) {
+  or_pair p = {m, n, r, h, bq, iq, dq, gcp, alpha_mode, gq};
   if (check_pair(&p) != OR_OK) return NAN;
   or_params t;
   if (params_init(&p, &t) != OR_OK) return NAN;
@@ -202,13 +210,15 @@ double oracle_forward_pair(int m, const uint8_t *r, const double *bq, const doub
 
 /*
  * Adjoint of one pair.  dy = d(loss)/d(log10 L).  Writes gradients of the loss w.r.t. the
- * Phred inputs: g_bq[m], g_iq[m], g_dq[m] (overwritten) and *g_gcp; returns log10 L.
+ * Phred inputs: g_bq[m], g_iq[m], g_dq[m] (overwritten), g_gq[m] (per-base gap-continuation
+ * values, overwritten; may be NULL) and *g_gcp = the sum of g_gq (the derivative for one gap-
+ * continuation value shared by every row); returns log10 L.
  */
 double oracle_backward_pair(int m, const uint8_t *r, const double *bq, const double *iq,
                             const double *dq, int n, const uint8_t *h, double gcp,
-                            int alpha_mode, double dy, double *g_bq, double *g_iq,
-                            double *g_dq, double *g_gcp) {
-  or_pair p = {m, n, r, h, bq, iq, dq, gcp, alpha_mode};
+                            int alpha_mode, const double *gq, double dy, double *g_bq,
+                            double *g_iq, double *g_dq, double *g_gq, double *g_gcp) {
+  or_pair p = {m, n, r, h, bq, iq, dq, gcp, alpha_mode, gq};
   if (check_pair(&p) != OR_OK) return NAN;
   or_params t;
   if (params_init(&p, &t) != OR_OK) return NAN;
@@ -216,7 +226,7 @@ double oracle_backward_pair(int m, const uint8_t *r, const double *bq, const dou
   double *SM = (double *)malloc(sizeof(double) * 3 * cells);
   double *A = (double *)calloc(6 * W, sizeof(double)); /* adjoint rows i+1 and i */
   int *e = (int *)malloc(sizeof(int) * (size_t)(m + 1));
-  double *gA = (double *)calloc(5 * (size_t)(m + 1), sizeof(double));
+  double *gA = (double *)calloc(7 * (size_t)(m + 1), sizeof(double));
   if (!SM || !A || !e || !gA) {
     free(SM);
     free(A);
@@ -231,7 +241,10 @@ double oracle_backward_pair(int m, const uint8_t *r, const double *bq, const dou
   double res = forward_rows(&p, &t, SM, SI, SD, e, &Lt, &csum);
   if (!(Lt > 0.0)) {
     /* L == 0: log-likelihood has no finite gradient. */
-    for (int i = 0; i < m; ++i) g_bq[i] = g_iq[i] = g_dq[i] = NAN;
+    for (int i = 0; i < m; ++i) {
+      g_bq[i] = g_iq[i] = g_dq[i] = NAN;
+      if (g_gq) g_gq[i] = NAN;
+    }
     *g_gcp = NAN;
     free(SM);
     free(A);
@@ -242,7 +255,7 @@ double oracle_backward_pair(int m, const uint8_t *r, const double *bq, const dou
   }
   /* Per-row accumulators of (1/L) dL/dtheta. */
   double *gal = gA, *gdel = gA + (m + 1), *gzet = gA + 2 * (m + 1), *gQ = gA + 3 * (m + 1);
-  double gbeta = 0.0, geps = 0.0;
+  double *gbeta = gA + 4 * (m + 1), *geps = gA + 5 * (m + 1);
   double *nM = A, *nI = A + W, *nD = A + 2 * W; /* row i+1 (normalised adjoints) */
   double *aM = A + 3 * W, *aI = A + 4 * W, *aD = A + 5 * W; /* row i */
   for (int i = m; i >= 1; --i) {
@@ -261,8 +274,10 @@ double oracle_backward_pair(int m, const uint8_t *r, const double *bq, const dou
         fromIv = nI[j];
       }
       double dnext = (j < n) ? aD[j + 1] : 0.0;
-      aD[j] = (t.beta * fromM) * down + t.eps * dnext;
-      aI[j] = seed + (t.beta * fromM + t.eps * fromIv) * down;
+      /* row i+1's transitions where the edge enters row i+1, row i's within row i */
+      const double beta1 = (i < m) ? t.beta[i + 1] : 0.0, eps1 = (i < m) ? t.eps[i + 1] : 0.0;
+      aD[j] = (beta1 * fromM) * down + t.eps[i] * dnext;
+      aI[j] = seed + (beta1 * fromM + eps1 * fromIv) * down;
       double alpha1 = (i < m) ? t.alpha[i + 1] : 0.0;
       double delta1 = (i < m) ? t.delta[i + 1] : 0.0;
       aM[j] = seed + (alpha1 * fromM + delta1 * fromIv) * down + t.zeta[i] * dnext;
@@ -274,14 +289,14 @@ double oracle_backward_pair(int m, const uint8_t *r, const double *bq, const dou
       double mdiag = Mp[j - 1], sdiag = Ip[j - 1] + Dp[j - 1];
       double a = aM[j] * lam * up;
       gal[i] += a * mdiag;
-      gbeta += a * sdiag;
-      double G = t.alpha[i] * mdiag + t.beta * sdiag;
+      gbeta[i] += a * sdiag;
+      double G = t.alpha[i] * mdiag + t.beta[i] * sdiag;
       double dlam_dQ = is_match(p.r[i - 1], p.h[j - 1]) ? -1.0 : 1.0 / 3.0;
       gQ[i] += aM[j] * up * G * dlam_dQ;
       gdel[i] += aI[j] * up * Mp[j];
-      geps += aI[j] * up * Ip[j];
+      geps[i] += aI[j] * up * Ip[j];
       gzet[i] += aD[j] * Mi[j - 1];
-      geps += aD[j] * Di[j - 1];
+      geps[i] += aD[j] * Di[j - 1];
     }
     double *tmp;
     tmp = nM; nM = aM; aM = tmp;
@@ -302,7 +317,14 @@ double oracle_backward_pair(int m, const uint8_t *r, const double *bq, const dou
       g_dq[i - 1] = k * (gzet[i] - gal[i]) * dP * t.zeta[i];
     }
   }
-  *g_gcp = k * (geps - gbeta) * dP * t.eps;
+  /* beta_i = 1 - eps_i: d/d gcp_i = (d/d eps_i - d/d beta_i) * dP * eps_i */
+  double gsum = 0.0;
+  for (int i = 1; i <= m; ++i) {
+    const double g = k * (geps[i] - gbeta[i]) * dP * t.eps[i];
+    if (g_gq) g_gq[i - 1] = g;
+    gsum += g;
+  }
+  *g_gcp = gsum;
   free(SM);
   free(A);
   free(e);
@@ -323,13 +345,14 @@ typedef struct {
   const int32_t *pair_read, *pair_hap;
   double gcp;
   int32_t alpha_mode;
+  const double *gq; /* per-base gap-continuation Phred values [sum m], or NULL */
 } oracle_batch;
 
 typedef struct {
   const oracle_batch *b;
   const double *dy;
   double *out;
-  double *gpair; /* per pair, 3*m values at pair_goff[p], or NULL */
+  double *gpair; /* per pair, 4*m values at pair_goff[p] (bq, iq, dq, gq), or NULL */
   const int64_t *goff;
   double *ggcp;
   int64_t next;
@@ -348,12 +371,14 @@ static void run_pair(job_t *J, int64_t p) {
   int m = (int)(r1 - r0), n = (int)(h1 - h0);
   if (!J->gpair) {
     J->out[p] = oracle_forward_pair(m, b->read_bases + r0, b->bq + r0, b->iq + r0, b->dq + r0, n,
-                                    b->hap_bases + h0, b->gcp, b->alpha_mode);
+                                    b->hap_bases + h0, b->gcp, b->alpha_mode,
+                                    b->gq ? b->gq + r0 : NULL);
   } else {
     double *g = J->gpair + J->goff[p];
     J->out[p] = oracle_backward_pair(m, b->read_bases + r0, b->bq + r0, b->iq + r0, b->dq + r0,
-                                     n, b->hap_bases + h0, b->gcp, b->alpha_mode, J->dy[p], g,
-                                     g + m, g + 2 * m, J->ggcp + p);
+                                     n, b->hap_bases + h0, b->gcp, b->alpha_mode,
+                                     b->gq ? b->gq + r0 : NULL, J->dy[p], g, g + m, g + 2 * m,
+                                     g + 3 * m, J->ggcp + p);
   }
 }
 
@@ -395,11 +420,13 @@ int oracle_forward_batch(const oracle_batch *b, double *out, int nthreads) {
 
 /*
  * Forward + adjoint over every pair.  dy[n_pairs] = d(loss)/d(log10 L_p).  Per-read gradient
- * arrays g_bq/g_iq/g_dq[sum m] are overwritten with the sum over pairs in pair order; *g_gcp
- * with the sum over pairs.  out[n_pairs] receives log10 L.
+ * arrays g_bq/g_iq/g_dq[sum m] (and g_gq[sum m] when not NULL: the per-base gap-continuation
+ * values) are overwritten with the sum over pairs in pair order; *g_gcp with the sum over
+ * pairs and rows.  out[n_pairs] receives log10 L.
  */
 int oracle_backward_batch(const oracle_batch *b, const double *dy, double *out, double *g_bq,
-                          double *g_iq, double *g_dq, double *g_gcp, int nthreads) {
+                          double *g_iq, double *g_dq, double *g_gq, double *g_gcp,
+                          int nthreads) {
   int64_t *goff = (int64_t *)malloc(sizeof(int64_t) * (size_t)(b->n_pairs + 1));
   double *ggcp = (double *)calloc((size_t)b->n_pairs + 1, sizeof(double));
   if (!goff || !ggcp) {
@@ -411,7 +438,7 @@ int oracle_backward_batch(const oracle_batch *b, const double *dy, double *out, 
   for (int64_t p = 0; p < b->n_pairs; ++p) {
     int32_t ri = b->pair_read[p];
     int64_t m = (ri >= 0 && ri < b->n_reads) ? b->read_off[ri + 1] - b->read_off[ri] : 0;
-    goff[p + 1] = goff[p] + 3 * m;
+    goff[p + 1] = goff[p] + 4 * m;
   }
   double *gpair = (double *)calloc((size_t)goff[b->n_pairs] + 1, sizeof(double));
   if (!gpair) {
@@ -429,7 +456,10 @@ int oracle_backward_batch(const oracle_batch *b, const double *dy, double *out, 
   J.ggcp = ggcp;
   run_all(&J, nthreads);
   int64_t total = b->read_off[b->n_reads];
-  for (int64_t i = 0; i < total; ++i) g_bq[i] = g_iq[i] = g_dq[i] = 0.0;
+  for (int64_t i = 0; i < total; ++i) {
+    g_bq[i] = g_iq[i] = g_dq[i] = 0.0;
+    if (g_gq) g_gq[i] = 0.0;
+  }
   double gg = 0.0;
   for (int64_t p = 0; p < b->n_pairs; ++p) {
     int32_t ri = b->pair_read[p];
@@ -441,6 +471,7 @@ int oracle_backward_batch(const oracle_batch *b, const double *dy, double *out, 
       g_bq[r0 + i] += g[i];
       g_iq[r0 + i] += g[m + i];
       g_dq[r0 + i] += g[2 * m + i];
+      if (g_gq) g_gq[r0 + i] += g[3 * m + i];
     }
     gg += ggcp[p];
   }

@@ -294,6 +294,95 @@ def test_alpha_mode_1_brute_force(seed):
         assert got == pytest.approx(math.log10(exact), abs=1e-12)
 
 
+# ------------------------------------------------- per-base gap-continuation track -------
+
+@pytest.mark.parametrize("seed", range(24))
+def test_per_base_gcp_brute_force(seed):
+    # a per-read-position gap continuation (eps_i, beta_i of the row being entered) against
+    # exact path enumeration with one eps per read position
+    rng = np.random.default_rng(9500 + seed)
+    m = int(rng.integers(1, 5))
+    n = int(rng.integers(1, 6))
+    alph = "ACGTN" if seed % 3 == 0 else "ACGT"
+    read, hap = rand_seq(rng, m, alph), rand_seq(rng, n, alph)
+    bq = rng.integers(0, 41, size=m).astype(float)
+    iq = rng.integers(3, 30, size=m).astype(float)
+    dq = rng.integers(3, 30, size=m).astype(float)
+    gq = rng.integers(1, 40, size=m).astype(float)
+    exact = brute.likelihood(read, hap, [Fraction(P(q)) for q in bq],
+                             [Fraction(P(q)) for q in iq], [Fraction(P(q)) for q in dq],
+                             [Fraction(P(q)) for q in gq])
+    got = oracle.forward_pair(read, bq, iq, dq, hap, gcp=10.0, gcp_q=gq)
+    if exact == 0:
+        assert got == -math.inf
+    else:
+        assert got == pytest.approx(math.log10(exact), abs=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_per_base_gcp_2x3_closed_form(seed):
+    # The 2x3 closed form with row-indexed beta: the start enters row 1 through beta_1, the
+    # deletion path M(1,1) -> D(1,2) -> M(2,3) returns to M through beta_2:
+    # L = (b1/3)[l11 l22 a2 + l23 (l12 a2 + b2 z1 l11) + d2 (l11 + l12 + l13)]
+    rng = np.random.default_rng(600 + seed)
+    read, hap = rand_seq(rng, 2), rand_seq(rng, 3)
+    bq = rng.integers(5, 41, size=2).astype(float)
+    iq = rng.integers(5, 40, size=2).astype(float)
+    dq = rng.integers(5, 40, size=2).astype(float)
+    gq = rng.uniform(2, 20, size=2)
+    Q, d, z = P(bq), P(iq), P(dq)
+    a = 1 - (d + z)
+    b1, b2 = 1 - P(gq[0]), 1 - P(gq[1])
+
+    def lam(i, j):
+        return (1 - Q[i - 1]) if read[i - 1] == hap[j - 1] else Q[i - 1] / 3
+
+    L = (b1 / 3) * (lam(1, 1) * lam(2, 2) * a[1]
+                    + lam(2, 3) * (lam(1, 2) * a[1] + b2 * z[0] * lam(1, 1))
+                    + d[1] * (lam(1, 1) + lam(1, 2) + lam(1, 3)))
+    got = oracle.forward_pair(read, bq, iq, dq, hap, gcp=10.0, gcp_q=gq)
+    assert got == pytest.approx(math.log10(L), abs=1e-13)
+
+
+def test_per_base_gcp_uniform_track_is_the_scalar():
+    # a track holding the scalar value everywhere gives the scalar path's results exactly, and
+    # its per-position gradients sum to the scalar d/dgcp
+    b = synth.random_pairs(51, 20, (1, 40), (1, 60), alphabet=b"ACGTN", qual_dtype=np.float32)
+    tot = int(b["read_off"][-1])
+    bt = dict(b, gcp_q=np.full(tot, b["gcp"], dtype=np.float32))
+    assert np.array_equal(oracle.forward_batch(bt), oracle.forward_batch(b))
+    dy = np.random.default_rng(1).uniform(-1, 1, len(b["pair_read"]))
+    y0, b0, i0, d0, g0 = oracle.backward_batch(b, dy)
+    y1, b1, i1, d1, gq = oracle.backward_batch(bt, dy)
+    for u, v in ((y0, y1), (b0, b1), (i0, i1), (d0, d1)):
+        assert np.array_equal(u, v)
+    assert gq.shape == (tot,)
+    assert np.sum(gq) == pytest.approx(g0, rel=1e-12, abs=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_per_base_gcp_adjoint_vs_central_differences(seed):
+    rng = np.random.default_rng(950 + seed)
+    m, n = int(rng.integers(1, 20)), int(rng.integers(1, 30))
+    hap = rand_seq(rng, n, "ACGTN")
+    read = hap[:m] if (seed % 2 == 0 and m <= n) else rand_seq(rng, m, "ACGTN")
+    bq = rng.uniform(2, 40, size=m)
+    iq = rng.uniform(15, 45, size=m)
+    dq = rng.uniform(15, 45, size=m)
+    gq = rng.uniform(3, 25, size=m)
+    y, gb, gi, gd, gg = oracle.backward_pair(read, bq, iq, dq, hap, gcp=10.0, dy=1.0, gcp_q=gq)
+    assert gg.shape == (m,)
+    for arr, g in ((bq, gb), (iq, gi), (dq, gd), (gq, gg)):
+        for i in range(m):
+            def fi(v, arr=arr, i=i):
+                a = arr.copy()
+                a[i] = v
+                args = [a if arr is x else x for x in (bq, iq, dq, gq)]
+                return oracle.forward_pair(read, args[0], args[1], args[2], hap, gcp=10.0,
+                                           gcp_q=args[3])
+            assert g[i] == pytest.approx(_fd(fi, arr[i]), rel=2e-5, abs=1e-9)
+
+
 def test_invalid_inputs_give_nan():
     assert math.isnan(oracle.forward_pair("AXG", [30] * 3, [45] * 3, [45] * 3, "ACG"))
     assert math.isnan(oracle.forward_pair("ACG", [30] * 3, [45] * 3, [45] * 3, "AC-"))
