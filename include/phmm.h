@@ -293,14 +293,17 @@ int phmm_grad_host(const phmm_batch *host_batch, const phmm_options *opt,
  * Arguments are those of phmm_batch (device memory, caller-owned) plus out_log10[P] and
  * out_flags[P] (device).  It scores every pair with the extended-range FP32 wavefront in one
  * lanes x rows group sized by the longest read (no length binning, no FP64 rescue: flags
- * are PHMM_FLAG_FP32 | PHMM_FLAG_EXTENDED, or PHMM_FLAG_INVALID for out-of-range pair ids).
- * Bases and qualities are not validated (use phmm_plan_create for that where allocation
- * is allowed).  It waits once on `stream` to read the batch sizes.
+ * are PHMM_FLAG_FP32 | PHMM_FLAG_EXTENDED, or PHMM_FLAG_INVALID with a NaN result for
+ * out-of-range pair ids).  The offsets are checked on the device (read_off[0] == hap_off[0]
+ * == 0, every read and haplotype non-empty); bases and qualities are not validated (use
+ * phmm_plan_create for that where allocation is allowed).  It waits once on `stream` to
+ * read the batch sizes and the offset check.
  *
  * Returns PHMM_ENOMEM if the batch's scratch (16 B per read base + 1 B per read base + the
- * padded haplotype codes, about 1 B per haplotype base + 32 B per haplotype) exceeds
+ * padded haplotype codes, about 1 B per haplotype base + 112 B per haplotype) exceeds
  * PHMM_NOALLOC_SCRATCH_BYTES, PHMM_ETOOLONG for a read longer than PHMM_MAX_READ_LEN,
- * PHMM_EINVAL for bad arguments, PHMM_ECUDA on a CUDA error.
+ * PHMM_EINVAL for bad arguments or offsets, PHMM_ECUDA on a CUDA error.  A batch without
+ * pairs returns PHMM_OK after the checks.
  *
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.  Every call

@@ -326,30 +326,41 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
     T Sfin = 0;
     int Efin = 0;
     bool done = false;
-    // Haplotype codes of the lane's columns over segment qq's steps, 3 bits per step (at
-    // step s lane t is at column s + 1 - t; columns outside 1..n take the null code).  Every
-    // lane reads its own, one segment ahead: no code exchange and no load on the steps'
-    // dependency chain.  The reverse sweep reuses them.
-    static_assert(3 * kSeg <= 31, "codes of a segment must fit one register");
-    auto seg_codes = [&](int qq) {
-      int cs = 0;
-      if (qq >= 0 && qq < nq) {
-        const int bb = qq < ramp ? qq : ramp + kSeg * (qq - ramp);
-        const int ll = qq < ramp ? 1 : kSeg;
+    // whether the lane's forward state is nonzero at the current checkpoint (kept with the
+    // checkpoint's exponent, so the reverse knows which segments hold forward values)
+    bool nzA;
+    {
+      T mx = fmax(st.Md, st.Sd);
 #pragma unroll
-        for (int u = 0; u < kSeg; ++u) {
-          const int64_t i = (int64_t)bb + u - t;  // 0-based haplotype position
-          const int c = (u < ll && i >= 0 && i < n) ? (int)fa.hcode[hs + i] : kNull;
-          cs |= c << (3 * u);
-        }
-      }
-      return cs;
+      for (int r = 0; r < K; ++r) mx = fmax(mx, st.I[r]);  // M and D start at zero
+      nzA = mx > (T)0;
+    }
+    // Haplotype codes of the lane's columns over segment qq's steps, one byte per step (at
+    // step s lane t is at column s + 1 - t; columns outside 1..n take the null code).  Every
+    // lane reads its own 8-byte window, one segment ahead: no code exchange and no load on
+    // the steps' dependency chain.  The reverse sweep reuses them.  The window starts at most
+    // 31 columns before column 1 and is clamped to start at column n + 1 at the latest, so it
+    // stays inside the NULLC guards around the haplotype's codes: no per-step bounds checks.
+    static_assert(kSeg <= 8 && kHapGuard >= 32 + 4, "codes of a segment: one 8-byte window");
+    constexpr uint64_t kNullCodes = 0x0505050505050505ull;
+    auto seg_codes = [&](int qq) -> uint64_t {
+      if (qq < 0 || qq >= nq || n <= 0) return kNullCodes;
+      const int bb = qq < ramp ? qq : ramp + kSeg * (qq - ramp);
+      int64_t i0 = (int64_t)bb - t;  // 0-based haplotype position of the window's first step
+      if (i0 > n) i0 = n;
+      const uintptr_t addr = (uintptr_t)(fa.hcode + hs + i0);
+      const uint32_t *w = reinterpret_cast<const uint32_t *>(addr & ~(uintptr_t)3);
+      const uint32_t sh = 8u * (uint32_t)(addr & 3);
+      const uint32_t w0 = w[0], w1 = w[1], w2 = w[2];
+      const uint32_t lo = __funnelshift_r(w0, w1, sh), hi = __funnelshift_r(w1, w2, sh);
+      return ((uint64_t)hi << 32) | lo;
     };
-    int segc = seg_codes(0);
+    auto code_at = [](uint64_t cs, int u) { return (int)((cs >> (8 * u)) & 0xff); };
+    uint64_t segc = seg_codes(0);
     for (int q = 0; q < nq; ++q) {
       const int b = q < ramp ? q : ramp + kSeg * (q - ramp);
       const int len = q < ramp ? 1 : kSeg;
-      const int cur = segc;
+      const uint64_t cur = segc;
       segc = seg_codes(q + 1);
       {
         T ck[CKW];
@@ -362,23 +373,22 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
         ck[3 * K] = st.Md;
         ck[3 * K + 1] = st.Sd;
         ck[3 * K + 2] = st.f;
-        ck[3 * K + 3] = int_bits<T>(st.E);
+        ck[3 * K + 3] = int_bits<T>(2 * st.E + (nzA ? 1 : 0));
 #pragma unroll
         for (int k = 3 * K + 4; k < CKW; ++k) ck[k] = 0;
         rec_store<T, CKW, true>(ckb + (size_t)q * 32 * CKW, lane, ck);
       }
       for (int u = 0; u < len; ++u) {
-        const int cu = (cur >> (3 * u)) & 7;
         T in3[3];
-        wf_step<T, L, K, true, true, true, false, true>(st, cu, t, bnd, eps, tblE, ap, dl, zt,
-                                                        ei, in3);
+        wf_step<T, L, K, true, true, true, false, true>(st, code_at(cur, u), t, bnd, eps, tblE,
+                                                        ap, dl, zt, ei, in3);
       }
       if (!done && b + len >= fin) {
         Sfin = st.acc;
         Efin = st.E;
         done = true;
       }
-      wf_rescale<T, L, K, kBias>(st, t);
+      nzA = wf_rescale<T, L, K, kBias>(st, t);
     }
     if (!done) {
       Sfin = st.acc;
@@ -419,11 +429,13 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
 
     // the lanes' codes of each segment's steps, loaded one segment ahead as in phase A
     segc = seg_codes(nq - 1);
+    bool nz_next = nzA;  // the state after the last segment
     for (int q = nq - 1; q >= 0; --q) {
       const int b = q < ramp ? q : ramp + kSeg * (q - ramp);
       const int len = q < ramp ? 1 : kSeg;
-      const int codes = segc;
+      const uint64_t codes = segc;
       segc = seg_codes(q - 1);
+      bool nzq;
       {
         T ck[CKW];
         rec_load<T, CKW, true>(ckb + (size_t)q * 32 * CKW, lane, ck);
@@ -436,16 +448,19 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
         st.Md = ck[3 * K];
         st.Sd = ck[3 * K + 1];
         st.f = ck[3 * K + 2];
-        st.E = bits_int<T>(ck[3 * K + 3]);
+        const int ef = bits_int<T>(ck[3 * K + 3]);
+        st.E = ef >> 1;
+        nzq = (ef & 1) != 0;
       }
       // bring the next (left) segment's checkpoint from DRAM towards L2 while this one runs
       if (q > 0 && lane == 0) prefetch_l2(ckb + (size_t)(q - 1) * 32 * CKW, 32 * CKW * sizeof(T));
-      T mxF = fmax(st.Md, st.Sd);
-#pragma unroll
-      for (int r = 0; r < K; ++r) mxF = fmax(mxF, fmax(st.M[r], fmax(st.I[r], st.D[r])));
+      // forward values in the lane over this segment: nonzero at its start or at its end (a
+      // lane's state turns nonzero once and stays so; power-of-two rescaling keeps zeros)
+      const bool nzF = nzq || nz_next;
+      nz_next = nzq;
       // recompute the segment, recording the lane's rows after each step (column b+u2+1-t)
       for (int u2 = 0; u2 < len; ++u2) {
-        const int cu = (codes >> (3 * u2)) & 7;
+        const int cu = code_at(codes, u2);
         T in3[3];
         wf_step<T, L, K, true, true, true, false, true>(st, cu, t, bnd, eps, tblE, ap, dl, zt,
                                                         ei, in3);
@@ -464,13 +479,10 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
       }
       const int EF = st.E;
       const T fS = bndS * Num<T>::exp2i(-EF);  // lane 0's boundary row in its own scale
-#pragma unroll
-      for (int r = 0; r < K; ++r) mxF = fmax(mxF, fmax(st.M[r], fmax(st.I[r], st.D[r])));
-      const bool nzF = mxF > (T)0;
       // reverse over the segment
       for (int u2 = len - 1; u2 >= 0; --u2) {
         const int64_t j = (int64_t)b + u2 + 1 - t;  // this lane's column at this step
-        const int c = (codes >> (3 * u2)) & 7;
+        const int c = code_at(codes, u2);
         // forward values of the lane's rows at column j: M, I, D/zeta (rec[r], [K+r], [2K+r])
         T rec[3 * K];
         if (u2 == len - 1) {
@@ -515,8 +527,13 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
         const bool nzB = as.nz || rU != (T)0 || rI != (T)0 || sd != (T)0;
         const bool live = real_lane && nzF && nzB;
         if (live && h > kHmax) hard = true;
-        if (live && h >= kHmin && h <= kHmax && h != H) {
-          // re-base the sums from 2^-H to 2^-h (all zero while H is unset); a shift beyond
+        // A step whose posterior scale is negligible (h < kHmin) adds its products at scale
+        // kHmin: each is then counted 2^(kHmin - h) times too large, yet stays below
+        // 2^(16 + kHmin) of a posterior, far under the rounding of the sums it joins.  Every
+        // lane runs the same code, with no per-step zeroing.
+        const int hq = h < kHmin ? kHmin : h;
+        if (live && hq <= kHmax && hq != H) {
+          // re-base the sums from 2^-H to 2^-hq (all zero while H is unset); a shift beyond
           // the type's exponent range is applied in two exact halves
           auto rebase = [&](T sc) {
 #pragma unroll
@@ -534,26 +551,18 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
             gED *= sc;
           };
           if (H != kNoScale) {
-            int d = H - h;
+            int d = H - hq;
             if (d > kHmax + 20 || d < -(kHmax + 20)) {
               rebase(Num<T>::exp2i(d / 2));
               d -= d / 2;
             }
             rebase(Num<T>::exp2i(d));
           }
-          H = h;
+          H = hq;
         }
-        // Products are added unless the step's posterior scale is negligible (h < kHmin on a
-        // live lane): such a lane zeroes its forward values for the step (every product has
-        // one as a factor), so all lanes of the warp run the same code.  Lanes that are not
-        // live add zeros (all forward or all adjoint values zero), garbage that is discarded
-        // (pad lanes) or garbage of a pair that goes to FP64 (h > kHmax): no per-row branch.
-        const bool quiet = live && h < kHmin;
-        if (quiet) {
-#pragma unroll
-          for (int k = 0; k < 3 * K; ++k) rec[k] = 0;
-        }
-        const T fSq = quiet ? (T)0 : fS;
+        // Lanes that are not live add zeros (all forward or all adjoint values zero), garbage
+        // that is discarded (pad lanes) or garbage of a pair that goes to FP64 (h > kHmax):
+        // no per-row branch.
         T ub = ubK, Ibl = rI;
         {
 #pragma unroll
@@ -561,13 +570,15 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
             const T apB = r == K - 1 ? apb : ap[r + 1];
             const T dlB = r == K - 1 ? dlb : dl[r + 1];
             const T eiB = r == K - 1 ? eib : ei[r + 1];
-            const T add = r == K - 1 ? sd : (T)0;
             const T uba = fabs(ub);       // u(r+1, j+1); u carries the emission's sign
             const T zD = zt[r] * as.Db[r];
             const T Mv = rec[r], Iv = rec[K + r], Dv = rec[2 * K + r];  // forward, column j
-            const T Mb = apB * uba + dlB * Ibl + zD + add;               // M^(r, j)
+            // M^(r, j); the last row of the last lane adds the seed 1/L (no addition of a
+            // zero elsewhere: x + 0 is not free in IEEE arithmetic)
+            const T Mb0 = fma(apB, uba, fma(dlB, Ibl, zD));
+            const T Mb = r == K - 1 ? Mb0 + sd : Mb0;
             // I^(r, j): one FMA on the row-to-row chain; eps x I^(r+1, j) again for the partial
-            const T Ib = fma(eiB, Ibl, uba + add);
+            const T Ib = fma(eiB, Ibl, r == K - 1 ? uba + sd : uba);
             const T Il = eiB * Ibl;
             const T Dn = uba + eps * as.Db[r];                           // D^(r, j)
             const T un = e[r] * Mb;                                      // u(r, j)
@@ -594,7 +605,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
             Ibl = Ib;
           }
           // lane 0's row above: u(0, j+1) times the boundary S = K0 D(0, j)
-          gS += fabs(ub) * fSq;
+          gS += fabs(ub) * fS;
         }
         as.Itop = Ibl;
         const int sf = b + u2 + 1;  // forward step just reversed

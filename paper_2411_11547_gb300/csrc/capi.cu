@@ -225,7 +225,7 @@ static void make_layout(phmm_plan *pl) {
   };
   L.rp = take(sizeof(RowParams) * std::max<int64_t>(pl->sum_m, 1));
   L.rcode = take(std::max<int64_t>(pl->sum_m, 1));
-  L.hcode = take((size_t)hap_start(pl->sum_n, pl->b.n_haps) + 64);
+  L.hcode = take((size_t)hap_code_bytes(pl->sum_n, pl->b.n_haps));
   L.key = take(4 * P);
   L.order = take(4 * P);
   // region zeroed at the start of every forward

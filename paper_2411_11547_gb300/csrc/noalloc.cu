@@ -31,25 +31,42 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char *g_addr[kMaxDevices];  // device address of g_noalloc_scratch, per device
 
-// Header at the start of the scratch: the longest read, written by k_max_read_len.
+// Header at the start of the scratch: the longest read and an error word, written by
+// k_check_offsets.
 struct Header {
   int32_t max_m;
-  int32_t pad[63];
+  uint32_t err;  // nonzero: the offsets are not non-decreasing from 0 with non-empty entries
+  int32_t pad[62];
 };
 
-__global__ void k_max_read_len(const int64_t *read_off, int64_t R, Header *h) {
+// Offset checks (the planned entry points make them on the host after copying the offsets;
+// here the offsets stay on the device): read_off[0] == hap_off[0] == 0, every read and
+// haplotype non-empty, haplotypes at most INT32_MAX / 2 long; and the longest read.  Bad
+// offsets would otherwise let the preparation kernels write past the scratch they were
+// sized for.
+__global__ void k_check_offsets(const int64_t *read_off, int64_t R, const int64_t *hap_off,
+                                int64_t H, Header *h) {
   int32_t mx = 0;
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R;
-       r += (int64_t)gridDim.x * blockDim.x) {
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tid == 0) bad = read_off[0] != 0 || hap_off[0] != 0;
+  for (int64_t r = tid; r < R; r += stride) {
     const int64_t m = read_off[r + 1] - read_off[r];
+    if (m <= 0) bad = true;
     const int32_t v = m < 0 ? 0 : (m > 1 << 30 ? 1 << 30 : (int32_t)m);
     mx = v > mx ? v : mx;
+  }
+  for (int64_t k = tid; k < H; k += stride) {
+    const int64_t n = hap_off[k + 1] - hap_off[k];
+    if (n <= 0 || n > INT32_MAX / 2) bad = true;
   }
   for (int o = 16; o > 0; o >>= 1) {
     const int32_t y = __shfl_down_sync(0xffffffffu, mx, o);
     mx = y > mx ? y : mx;
   }
   if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(&h->max_m, mx);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&h->err, 1u);
 }
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -86,20 +103,23 @@ extern "C" int phmm_forward_noalloc(const phmm_batch *batch, double *out_log10,
     scratch = g_addr[dev];
   }
 
-  // sizes: total read and haplotype bases, and the longest read (one wait on `stream`)
+  // sizes: total read and haplotype bases, the longest read and the offset checks (one wait
+  // on `stream`)
   Header *hdr = (Header *)scratch;
   int64_t sum_m = 0, sum_n = 0;
-  int32_t max_m = 0;
+  int32_t hh[2] = {0, 0};  // max_m, err
   if (cudaMemsetAsync(hdr, 0, sizeof(Header), s) != cudaSuccess) return PHMM_ECUDA;
-  k_max_read_len<<<64, 256, 0, s>>>(b.read_off, b.n_reads, hdr);
+  k_check_offsets<<<64, 256, 0, s>>>(b.read_off, b.n_reads, b.hap_off, b.n_haps, hdr);
   if (cudaGetLastError() != cudaSuccess) return PHMM_ECUDA;
   if (cudaMemcpyAsync(&sum_m, b.read_off + b.n_reads, 8, cudaMemcpyDeviceToHost, s) !=
           cudaSuccess ||
       cudaMemcpyAsync(&sum_n, b.hap_off + b.n_haps, 8, cudaMemcpyDeviceToHost, s) !=
           cudaSuccess ||
-      cudaMemcpyAsync(&max_m, &hdr->max_m, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(hh, hdr, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return PHMM_ECUDA;
+  const int32_t max_m = hh[0];
+  if (hh[1] != 0) return PHMM_EINVAL;
   if (sum_m <= 0 || sum_n <= 0 || max_m <= 0) return PHMM_EINVAL;
   if (max_m > PHMM_MAX_READ_LEN) return PHMM_ETOOLONG;
 
@@ -107,7 +127,7 @@ extern "C" int phmm_forward_noalloc(const phmm_batch *batch, double *out_log10,
   const size_t o_rp = up256(sizeof(Header));
   const size_t o_rcode = up256(o_rp + sizeof(RowParams) * (size_t)sum_m);
   const size_t o_hcode = up256(o_rcode + (size_t)sum_m);
-  const size_t end = o_hcode + (size_t)hap_start(sum_n, b.n_haps) + 64;
+  const size_t end = o_hcode + (size_t)hap_code_bytes(sum_n, b.n_haps);
   if (end > (size_t)PHMM_NOALLOC_SCRATCH_BYTES) return PHMM_ENOMEM;
   RowParams *rp = (RowParams *)(scratch + o_rp);
   uint8_t *rcode = scratch + o_rcode, *hcode = scratch + o_hcode;

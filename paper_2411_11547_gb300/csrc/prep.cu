@@ -98,16 +98,19 @@ __global__ void k_prep_reads(const uint8_t *bases, const void *bq, const void *i
   }
 }
 
-// One warp per haplotype: codes into hcode[hap_start(h) ...], NULLC up to the 16-byte end.
+// One warp per haplotype: codes into hcode[hap_start(h) ...], NULLC up to the 16-byte end,
+// and kHapGuard bytes of NULLC before and after (guards of neighbouring haplotypes may
+// overlap; both write NULLC there).
 __global__ void k_prep_haps(const uint8_t *bases, const int64_t *hap_off, int64_t H,
                             uint8_t *hcode) {
   const int lane = threadIdx.x & 31;
+  constexpr int kG = kHapGuard / 16;
   for (int64_t h = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; h < H;
        h += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const int64_t o = hap_off[h], n = hap_off[h + 1] - o;
     const int64_t hs = hap_start(o, h);
     const int64_t chunks = (n + 15) >> 4;
-    for (int64_t k = lane; k < chunks; k += 32) {
+    for (int64_t k = lane - kG; k < chunks + kG; k += 32) {
       uint32_t w[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -116,7 +119,7 @@ __global__ void k_prep_haps(const uint8_t *bases, const int64_t *hap_off, int64_
         for (int b = 0; b < 4; ++b) {
           const int64_t j = k * 16 + q * 4 + b;
           int c = kNull;
-          if (j < n) {
+          if (j >= 0 && j < n) {
             c = base_code(bases[o + j]);
             if (c < 0) c = kN;
           }

@@ -63,10 +63,18 @@ struct Num<double> {
   }
 };
 
-// Start of haplotype h inside the code buffer: 16-byte aligned, with room for the NULLC
-// padding up to the next 16-byte boundary (closed form, so no scan is needed).
+// Start of haplotype h inside the code buffer: 16-byte aligned (closed form, so no scan is
+// needed).  Every haplotype has at least kHapGuard bytes of NULLC before its first code and
+// after its last (the preparation kernel writes them), so a lane may read a window of codes
+// that starts up to kHapGuard - 4 columns before column 1 or ends up to kHapGuard - 4 past
+// column n without a bounds check.
+constexpr int kHapGuard = 48;
 __host__ __device__ __forceinline__ int64_t hap_start(int64_t hap_off_h, int64_t h) {
-  return (hap_off_h + 32 * h + 15) & ~(int64_t)15;
+  return (hap_off_h + (2 * kHapGuard + 16) * h + kHapGuard + 15) & ~(int64_t)15;
+}
+// Bytes of the code buffer for haplotypes of sum_n bases in total.
+__host__ __device__ __forceinline__ int64_t hap_code_bytes(int64_t sum_n, int64_t H) {
+  return hap_start(sum_n, H) + 2 * kHapGuard;
 }
 
 // Shared-memory row stride (elements) of one lane's emission rows: a lane's 16-byte chunks
@@ -112,7 +120,9 @@ __device__ __forceinline__ void load_rows(const T *src, T (&e)[K]) {
     }
   }
   if constexpr (K % VW == 2 && sizeof(T) == 4) {
-    float2 v = *reinterpret_cast<const float2 *>(src + K - 2);
+    // the row is padded to a whole vector: one 128-bit load (a 64-bit load at the odd 16-byte
+    // lane stride would put two lanes of a half-warp on the same bank)
+    float4 v = *reinterpret_cast<const float4 *>(src + K - 2);
     e[K - 2] = v.x;
     e[K - 1] = v.y;
   }
@@ -241,9 +251,9 @@ __device__ __forceinline__ void wf_step(WfState<T, K> &st, int cu, int t, T bnd,
 
 // Per-lane renormalisation by a power of two (exact).  A lane that holds only zeros (the
 // wavefront has not reached it) takes the exponent that makes the next values from the lane
-// above arrive near 1.
+// above arrive near 1.  Returns whether the lane's state is nonzero.
 template <typename T, int L, int K, int kBias>
-__device__ __forceinline__ void wf_rescale(WfState<T, K> &st, int t) {
+__device__ __forceinline__ bool wf_rescale(WfState<T, K> &st, int t) {
   constexpr unsigned FULL = 0xffffffffu;
   T mx = st.Md > st.Sd ? st.Md : st.Sd;
 #pragma unroll
@@ -270,6 +280,7 @@ __device__ __forceinline__ void wf_rescale(WfState<T, K> &st, int t) {
   if (zero && t > 0)
     st.E = Eup - kBias * (K - 1) + (xbu > (T)0 ? Num<T>::ilog2(xbu) : 0);
   st.f = Num<T>::exp2i(t == 0 ? -st.E : Eup - st.E - kBias * (K - 1));
+  return !zero;
 }
 
 // ---- packed FP32 path (fma.rn.f32x2 / mul.rn.f32x2: two lane operations per instruction,

@@ -1,8 +1,14 @@
 """GPU adjoint vs the FP64 oracle adjoint, through the C ABI.
 
 Bar: gradients within 1e-3 relative.  An element whose reference is tiny compared with the
-rest of its array is compared with an absolute floor of 1e-5 x max|reference| of that array
-(FP32 sums of posterior-scale terms carry an absolute, not relative, rounding error).
+rest of ITS READ is compared with an absolute floor of 1e-4 x the largest |reference| of the
+same track over the same read.  The floor follows from the arithmetic: each element is a
+difference of sums of posterior-scale products (e.g. d/dbq = 0.1 (A1 Q/(1-Q) - A2) with
+A1 + A2 the M occupancy of the row), and the FP32 forward and adjoint values behind those
+products carry relative errors that grow with the columns swept, up to about n 2^-24
+(2e-5 at n = 300; 1.2e-5 of the read's largest element was measured on a 3-row read).  An
+element that nearly cancels keeps that error in absolute terms, so it cannot meet a
+relative bar; the floor is five times the measured error.
 """
 import numpy as np
 import pytest
@@ -12,7 +18,7 @@ from paper_2411_11547_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-RTOL, FLOOR = 1e-3, 1e-5
+RTOL, FLOOR = 1e-3, 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -26,11 +32,23 @@ def phmm():
     return ph
 
 
-def grad_close(got, want, name):
+def read_floor(want, read_off):
+    """FLOOR x max |want| over each element's own read (read_off: that read's offsets into
+    `want`)."""
+    a = np.abs(np.asarray(want, dtype=np.float64))
+    ro = np.asarray(read_off, dtype=np.int64)
+    lens = np.diff(ro)
+    keep = lens > 0
+    mx = np.zeros(len(lens))
+    mx[keep] = np.maximum.reduceat(a, ro[:-1][keep])
+    return FLOOR * np.maximum(np.repeat(mx, lens), 1e-300)
+
+
+def grad_close(got, want, name, read_off):
     got = np.asarray(got, dtype=np.float64)
     want = np.asarray(want, dtype=np.float64)
     assert np.all(np.isfinite(got)), f"{name}: non-finite"
-    tol = RTOL * np.abs(want) + FLOOR * max(np.abs(want).max(), 1e-300)
+    tol = RTOL * np.abs(want) + read_floor(want, read_off)
     bad = np.abs(got - want) > tol
     if bad.any():
         i = np.argmax(np.abs(got - want) - tol)
@@ -62,9 +80,10 @@ def check_against_oracle(ph, b, dy, **opt):
             ext = (fl & ph.FLAG_EXTENDED) != 0
             one = ((fl & ph.FLAG_FP32) != 0) ^ ((fl & ph.FLAG_RESCUED64) != 0)
             assert np.all(ext & one & ((fl & ph.FLAG_INVALID) == 0)), np.unique(fl)
-        grad_close(gb, wb, f"d/dbq fused={fused}")
-        grad_close(gi, wi, f"d/diq fused={fused}")
-        grad_close(gd, wd, f"d/ddq fused={fused}")
+        ro = b["read_off"]
+        grad_close(gb, wb, f"d/dbq fused={fused}", ro)
+        grad_close(gi, wi, f"d/diq fused={fused}", ro)
+        grad_close(gd, wd, f"d/ddq fused={fused}", ro)
         assert abs(gg - wg) <= RTOL * abs(wg) + 1e-9, (fused, gg, wg)
 
 
@@ -195,9 +214,10 @@ def test_autograd_function(phmm):
     wy, wb, wi, wd, wg = oracle.backward_batch(b, w)
     assert np.all(np.abs(y.detach().cpu().numpy() - wy) <= 1e-3)
     assert flags.dtype == torch.uint8 and not flags.requires_grad
-    grad_close(bq.grad.cpu().numpy(), wb, "d/dbq")
-    grad_close(iq.grad.cpu().numpy(), wi, "d/diq")
-    grad_close(dq.grad.cpu().numpy(), wd, "d/ddq")
+    ro = b["read_off"]
+    grad_close(bq.grad.cpu().numpy(), wb, "d/dbq", ro)
+    grad_close(iq.grad.cpu().numpy(), wi, "d/diq", ro)
+    grad_close(dq.grad.cpu().numpy(), wd, "d/ddq", ro)
     assert abs(float(gcp.grad) - wg) <= RTOL * abs(wg) + 1e-9
 
 
@@ -241,16 +261,17 @@ def test_c4_adjoint_full_size_sampled_regions(phmm):
     wy, wb, wi, wd, wg = oracle.backward_batch(sb, dy[pairs])
     ro = b["read_off"]
     idx = np.concatenate([np.arange(ro[r], ro[r + 1]) for r in reads])
-    grad_close(gb[idx], wb[idx], "d/dbq")
-    grad_close(gi[idx], wi[idx], "d/diq")
-    grad_close(gd[idx], wd[idx], "d/ddq")
+    sro = np.concatenate([[0], np.cumsum(ro[reads + 1] - ro[reads])])
+    grad_close(gb[idx], wb[idx], "d/dbq", sro)
+    grad_close(gi[idx], wi[idx], "d/diq", sro)
+    grad_close(gd[idx], wd[idx], "d/ddq", sro)
     # the fused step on the same plan: log10 L of the sampled pairs and the same gradients
     y, _ = plan.forward_partials()
     fb, fi, fd, fg = plan.backward_partials(torch.as_tensor(dy, device="cuda"))
     assert np.all(np.abs(y.cpu().numpy()[pairs] - wy) <= 1e-3)
-    grad_close(fb.cpu().numpy()[idx], wb[idx], "fused d/dbq")
-    grad_close(fi.cpu().numpy()[idx], wi[idx], "fused d/diq")
-    grad_close(fd.cpu().numpy()[idx], wd[idx], "fused d/ddq")
+    grad_close(fb.cpu().numpy()[idx], wb[idx], "fused d/dbq", sro)
+    grad_close(fi.cpu().numpy()[idx], wi[idx], "fused d/diq", sro)
+    grad_close(fd.cpu().numpy()[idx], wd[idx], "fused d/ddq", sro)
 
 
 def test_fused_step_empty_batch(phmm):
@@ -283,7 +304,8 @@ def test_every_pair_in_fp64(phmm, fused):
     if fused:
         assert np.all(fl == (phmm.FLAG_RESCUED64 | phmm.FLAG_EXTENDED))
         assert np.all(np.abs(y - wy) <= 1e-9)
-    grad_close(gb, wb, "d/dbq")
-    grad_close(gi, wi, "d/diq")
-    grad_close(gd, wd, "d/ddq")
+    ro = b["read_off"]
+    grad_close(gb, wb, "d/dbq", ro)
+    grad_close(gi, wi, "d/diq", ro)
+    grad_close(gd, wd, "d/ddq", ro)
     assert abs(gg - wg) <= 1e-6 * abs(wg) + 1e-9, (gg, wg)

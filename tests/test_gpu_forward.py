@@ -199,9 +199,68 @@ def test_invalid_inputs_are_rejected(phmm):
     assert e.value.status == phmm.PHMM_ETOOLONG
     plan = phmm.Plan(phmm.DeviceBatch(b))
     import ctypes
-    rc = phmm.lib().phmm_forward(plan.handle, ctypes.c_void_p(plan._ws_ptr), 16,
-                                 ctypes.c_void_p(0), ctypes.c_void_p(0), None)
-    assert rc in (phmm.PHMM_ENOMEM, phmm.PHMM_EINVAL)
+    import torch
+    P = len(b["pair_read"])
+    out = torch.empty(P, dtype=torch.float64, device="cuda")
+    fl = torch.empty(P, dtype=torch.uint8, device="cuda")
+    ws = ctypes.c_void_p(plan._ws_ptr)
+    # a workspace one byte short of phmm_workspace_bytes, everything else valid: PHMM_ENOMEM
+    for fn in (phmm.lib().phmm_forward, phmm.lib().phmm_forward_partials):
+        rc = fn(plan.handle, ws, plan.ws_bytes - 1, ctypes.c_void_p(out.data_ptr()),
+                ctypes.c_void_p(fl.data_ptr()), None)
+        assert rc == phmm.PHMM_ENOMEM
+    # enough workspace but no output arrays: PHMM_EINVAL; a misaligned workspace: PHMM_EINVAL
+    rc = phmm.lib().phmm_forward(plan.handle, ws, plan.ws_bytes, ctypes.c_void_p(0),
+                                 ctypes.c_void_p(0), None)
+    assert rc == phmm.PHMM_EINVAL
+    rc = phmm.lib().phmm_forward(plan.handle, ctypes.c_void_p(plan._ws_ptr + 16), plan.ws_bytes,
+                                 ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(fl.data_ptr()),
+                                 None)
+    assert rc == phmm.PHMM_EINVAL
+    # the same plan with the full workspace works
+    rc = phmm.lib().phmm_forward(plan.handle, ws, plan.ws_bytes, ctypes.c_void_p(out.data_ptr()),
+                                 ctypes.c_void_p(fl.data_ptr()), None)
+    assert rc == phmm.PHMM_OK
+    torch.cuda.synchronize()
+    check(out.cpu().numpy(), fl.cpu().numpy(), oracle.forward_batch(b), phmm)
+
+
+def test_extended_range_fp64_untiled(phmm):
+    """Pairs beyond the FP64 range of K0 = 2^1020 (log10 L < -597) under the paper's plain
+    FP32 first line: FP32 underflows, the FP64 rescue underflows too, and the per-lane-
+    exponent FP64 kernels (32 lanes x 4 / 8 / 16 rows, no row tiles) finish them.  Unrelated
+    reads with Phred-150 bases and gap opens and a Phred-150 gap continuation cost about 7
+    log10 units per row (a mismatch 15.5, a gap 15 plus 15 per base)."""
+    rng = np.random.default_rng(77)
+    regs = []
+    for m in [100, 120, 128, 140, 200, 256, 300, 380, 450, 512]:
+        for rep in range(3):
+            n = int(rng.integers(200, 700))
+            hap = synth.ACGT[rng.integers(0, 4, n)]
+            read = synth.ACGT[rng.integers(0, 4, m)]
+            regs.append(([hap], [read], [np.full(m, 150)], [np.full(m, 150)], [np.full(m, 150)]))
+    # and some ordinary related pairs in the same batch (FP32 or plain FP64 rescue)
+    short = synth.random_pairs(78, 40, (30, 300), (300, 500), related=1.0)
+    b = synth._assemble(regs, 150.0, "deep")
+    for k in ("read_bases", "base_q", "ins_q", "del_q", "hap_bases"):
+        b[k] = np.concatenate([b[k], short[k]])
+    b["read_off"] = np.concatenate([b["read_off"], b["read_off"][-1] + short["read_off"][1:]])
+    b["hap_off"] = np.concatenate([b["hap_off"], b["hap_off"][-1] + short["hap_off"][1:]])
+    b["pair_read"] = np.concatenate([b["pair_read"], short["pair_read"] + len(regs)]).astype(np.int32)
+    b["pair_hap"] = np.concatenate([b["pair_hap"], short["pair_hap"] + len(regs)]).astype(np.int32)
+    want = oracle.forward_batch(b)
+    deep = np.arange(len(regs))
+    assert np.all(want[deep] < -597.1), want[deep].max()
+    got, flags, plan = run(phmm, b, first_line=0, use_graph=0)
+    counts = plan.rescue_counts()
+    assert counts[1] >= len(regs), counts
+    ext64 = phmm.FLAG_RESCUED64 | phmm.FLAG_EXTENDED
+    assert np.all(flags[deep] == ext64), np.unique(flags[deep])
+    # every untiled FP64 group ran: reads up to 128, 256 and 512 rows
+    rl = np.diff(b["read_off"])[b["pair_read"]]
+    for lo, hi in ((1, 128), (129, 256), (257, 512)):
+        assert np.any((flags == ext64) & (rl >= lo) & (rl <= hi)), (lo, hi)
+    check(got, flags, want, phmm)
 
 
 def test_c4_sampled_pairs_full_size_launch(phmm):

@@ -91,9 +91,9 @@ def test_grad_host_matches_oracle_and_whole_batch(phmm, subset_cells):
     if subset_cells == 300_000:
         wy, wb, wi, wd, wg = oracle.backward_batch(b, dL)
         assert np.all(np.abs(y - wy) <= 1e-3)
-        grad_close(gb, wb, "d/dbq")
-        grad_close(gi, wi, "d/diq")
-        grad_close(gd, wd, "d/ddq")
+        grad_close(gb, wb, "d/dbq", b["read_off"])
+        grad_close(gi, wi, "d/diq", b["read_off"])
+        grad_close(gd, wd, "d/ddq", b["read_off"])
         assert abs(gg - wg) <= 1e-3 * abs(wg) + 1e-9
 
 
