@@ -146,9 +146,12 @@ struct AdjState {
 // Renormalise the adjoints of a lane by a power of two; a lane that holds only zeros takes
 // the exponent that makes the next values from the lane below arrive near 1.
 // `apply` selects the lanes that renormalise now (the exchange runs on every lane).
+// keep: the lane prefers the exponent Ek (which keeps its posterior scale, and so the scale
+// of its partial sums, unchanged) whenever that leaves its largest adjoint within 2^+-24;
+// otherwise it normalises the largest to [1, 2).
 template <typename T, int L, int K, int kBias>
 __device__ __forceinline__ void adj_rescale(AdjState<T, K> &as, int t, T S, int ES,
-                                            bool apply = true) {
+                                            bool apply = true, bool keep = false, int Ek = 0) {
   constexpr unsigned FULL = 0xffffffffu;
   T mx = fmax(as.Itop, fabs(as.diagU));
 #pragma unroll
@@ -156,7 +159,8 @@ __device__ __forceinline__ void adj_rescale(AdjState<T, K> &as, int t, T S, int 
   const bool zero = !(mx > (T)0);
   if (apply) as.nz = !zero;
   if (apply && !zero) {
-    const int En = as.EB + Num<T>::ilog2(mx);
+    int En = as.EB + Num<T>::ilog2(mx);
+    if (keep && Ek - En <= 24 && En - Ek <= 24) En = Ek;
     const T sc = Num<T>::exp2i(as.EB - En);
 #pragma unroll
     for (int r = 0; r < K; ++r) {
@@ -430,6 +434,10 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
     // the lanes' codes of each segment's steps, loaded one segment ahead as in phase A
     segc = seg_codes(nq - 1);
     bool nz_next = nzA;  // the state after the last segment
+    // A segment's closing renormalisation is applied at the start of the next segment's
+    // reverse, when that segment's forward exponent EF is known: a lane then keeps
+    // EF + EB = H where it can, so its partial sums need no re-basing.
+    bool pend = false;
     for (int q = nq - 1; q >= 0; --q) {
       const int b = q < ramp ? q : ramp + kSeg * (q - ramp);
       const int len = q < ramp ? 1 : kSeg;
@@ -479,6 +487,9 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
       }
       const int EF = st.E;
       const T fS = bndS * Num<T>::exp2i(-EF);  // lane 0's boundary row in its own scale
+      if (__any_sync(FULL, pend))
+        adj_rescale<T, L, K, kBias>(as, t, okS ? S : (T)0, ES, pend, H != kNoScale, H - EF);
+      pend = false;
       // reverse over the segment
       for (int u2 = len - 1; u2 >= 0; --u2) {
         const int64_t j = (int64_t)b + u2 + 1 - t;  // this lane's column at this step
@@ -609,7 +620,12 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
         }
         as.Itop = Ibl;
         const int sf = b + u2 + 1;  // forward step just reversed
-        const bool apply = sf <= fin && (u2 == 0 || sf > fin - ramp_b);
+        // Inside the adjoint's ramp (the first ramp_b steps from the pair's last column, a
+        // window set by the pair alone) a lane without adjoint mass renormalises after every
+        // step, to adopt the exponent of the values about to arrive; every lane renormalises
+        // at the segment's end (deferred to the next segment's start).
+        const bool apply = sf <= fin && sf > fin - ramp_b && !as.nz;
+        if (u2 == 0) pend = sf <= fin && !apply;
         if (__any_sync(FULL, apply)) adj_rescale<T, L, K, kBias>(as, t, okS ? S : (T)0, ES, apply);
       }
     }
