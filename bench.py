@@ -193,14 +193,27 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="use the built-in group tables instead of phmm_autotune's")
+    ap.add_argument("--shard", action="store_true",
+                    help="strong scaling: the ranks split ONE batch by read (every read's "
+                         "pairs on one rank) and sum d/dgcp with one all-reduce per step; "
+                         "default: every rank scores its own batch of the same shape")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     ws, rank, local = dist_env()
     from paper_2411_11547_gb300 import synth
     seed_base = {"c4_persistent": 4, "c1_batched": 1, "c3_grad": 3}[args.workload]
-    # weak scaling: every rank scores its own batch of the same shape (seeds per rank)
-    batch = synth.make(args.workload, seed=seed_base + 1000 * rank)
+    if args.shard:
+        # strong scaling: one batch, split by read over the ranks (shard.py)
+        from paper_2411_11547_gb300 import shard
+        full = synth.make(args.workload, seed=seed_base)
+        full_cells = synth.cells(full)
+        full_pairs = len(full["pair_read"])
+        batch, _, _ = shard.shard(full, rank, ws)
+        del full
+    else:
+        # weak scaling: every rank scores its own batch of the same shape (seeds per rank)
+        batch = synth.make(args.workload, seed=seed_base + 1000 * rank)
     if args.impl == "reference":
         return run_reference(args, batch, ws, rank)
 
@@ -248,7 +261,12 @@ def main():
     # adjoint sweep) and the FP64 per-read reduction weighted by dL
     def step():
         plan.forward_partials(out, flags)
-        return plan.backward_partials(dL)
+        g = plan.backward_partials(dL)
+        if args.shard and dist is not None:
+            # the one cross-rank sum of the sharded step: d/dgcp (8 bytes, in stream order)
+            from paper_2411_11547_gb300 import shard as _sh
+            _sh.allreduce_tensor_(g[3])
+        return g
 
     # the same step as two independent calls: the forward graph, then the whole backward
     def step_two_call():
@@ -462,7 +480,7 @@ def main():
         ms, ms_fwd, ms_two = float(t[0]), float(t[1]), float(t[3])
         if e2e:
             e2e["ms_per_step"] = float(t[2])
-    total_cells = cells * ws
+    total_cells = full_cells if args.shard else cells * ws
     value = total_cells / (ms * 1e-3) / 1e9
     fwd_gcups = total_cells / (ms_fwd * 1e-3) / 1e9
     if e2e:
@@ -487,16 +505,19 @@ def main():
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "strong" if args.shard else "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {WORKLOAD_DESC[args.workload]}",
-                   "pairs": P * ws, "cells": total_cells,
+                   "pairs": full_pairs if args.shard else P * ws, "cells": total_cells,
                    "step": ("log10 L and d(loss)/d(quals, gcp) of every pair with dL = 1: "
                             "phmm_forward_partials (the adjoint sweep's own forward gives "
                             "log10 L; pairs it cannot represent finished in FP64) + "
                             "phmm_backward_partials (FP64 per-read reduction weighted by dL)"),
                    "first_line": "FP32 with per-lane exponents (FP64 rescue when unrepresentable)",
-                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"weak x{ws}",
+                   "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": (f"one batch split by read over {ws} ranks (d/dgcp "
+                                   f"all-reduced per step)" if args.shard else f"weak x{ws}"),
                    "group_tables": ("built-in" if args.no_tune else
                                     f"phmm_autotune (32768-pair samples per 16-row read-length "
                                     f"range, {t_tune:.2f} s, outside the timed region)"),

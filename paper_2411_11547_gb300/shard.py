@@ -67,7 +67,36 @@ def shard(batch, rank: int, world: int):
     }
     if "alpha_mode" in batch:
         sub["alpha_mode"] = batch["alpha_mode"]
+    if batch.get("gcp_q") is not None:
+        sub["gcp_q"] = np.ascontiguousarray(batch["gcp_q"][b0:b1])
     return sub, pairs, (lo, hi)
+
+
+def sharded_step(batch, dL, rank: int, world: int, compute, group=None):
+    """One training step of `batch` sharded over `world` ranks, from this rank's side.
+
+    The rank takes its shard (contiguous reads, every pair of those reads), runs
+    compute(sub_batch, dL of the shard's pairs) -> (log10 L [shard pairs], d_base_q, d_ins_q,
+    d_del_q [shard read bases], d_gcp), and adds d_gcp over the ranks (the one exchange).
+    Returns a dict: "pairs" (global pair ids of the shard), "bases" (the global read-base
+    range (b0, b1) its gradients cover), "log10", "d_base_q", "d_ins_q", "d_del_q" (the
+    shard's values) and "d_gcp" (the sum over every rank).  Each global array is the
+    concatenation of the ranks' slices: no rank's slice overlaps another's.
+    """
+    sub, pairs, (lo, hi) = shard(batch, rank, world)
+    y, gb, gi, gd, gg = compute(sub, np.asarray(dL)[pairs])
+    ro = np.asarray(batch["read_off"], dtype=np.int64)
+    return {"pairs": pairs, "bases": (int(ro[lo]), int(ro[hi])), "log10": y, "d_base_q": gb,
+            "d_ins_q": gi, "d_del_q": gd, "d_gcp": allreduce_scalar(gg, group)}
+
+
+def allreduce_tensor_(t, group=None):
+    """Sum a tensor in place over the default (or given) process group (no host wait with
+    NCCL); identity without one."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    return t
 
 
 def allreduce_scalar(x, group=None):

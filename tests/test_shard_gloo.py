@@ -88,3 +88,50 @@ def test_two_ranks_gloo_match_unsharded(tmp_path):
     np.testing.assert_allclose(full[P + tot:P + 2 * tot], gi, rtol=1e-10, atol=1e-14)
     np.testing.assert_allclose(full[P + 2 * tot:], gd, rtol=1e-10, atol=1e-14)
     assert abs(float(np.load(tmp_path / "dgcp.npy")[0]) - gg) <= 1e-10 * abs(gg)
+
+
+def _worker_step(rank, world, port, out_dir):
+    """The library's orchestration (shard.sharded_step) with the oracle as each rank's compute:
+    partition, per-rank step, placement of the results and the d/dgcp sum over ranks."""
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        b = synth.c1_batched(regions=7)
+        dy = np.random.default_rng(1).uniform(-1, 1, len(b["pair_read"]))
+        r = shard.sharded_step(b, dy, rank, world,
+                               lambda sub, d: oracle.backward_batch(sub, d, nthreads=2))
+        np.savez(os.path.join(out_dir, f"rank{rank}.npz"), pairs=r["pairs"],
+                 bases=np.array(r["bases"]), y=r["log10"], gb=r["d_base_q"], gi=r["d_ins_q"],
+                 gd=r["d_del_q"], gg=np.array([r["d_gcp"]]))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_step_orchestration_gloo(tmp_path, world):
+    import torch.multiprocessing as mp
+    port = _free_port()
+    mp.start_processes(_worker_step, args=(world, port, str(tmp_path)), nprocs=world,
+                       join=True, start_method="spawn")
+    b = synth.c1_batched(regions=7)
+    dy = np.random.default_rng(1).uniform(-1, 1, len(b["pair_read"]))
+    y, gb, gi, gd, gg = oracle.backward_batch(b, dy, nthreads=2)
+    tot = int(b["read_off"][-1])
+    got_y = np.full(len(y), np.nan)
+    got = [np.full(tot, np.nan) for _ in range(3)]
+    for k in range(world):
+        r = np.load(tmp_path / f"rank{k}.npz")
+        assert np.all(np.isnan(got_y[r["pairs"]]))  # every pair on exactly one rank
+        got_y[r["pairs"]] = r["y"]
+        b0, b1 = (int(x) for x in r["bases"])
+        for arr, part in zip(got, (r["gb"], r["gi"], r["gd"])):
+            assert np.all(np.isnan(arr[b0:b1]))  # every read base on exactly one rank
+            arr[b0:b1] = part
+        # every rank holds the same d/dgcp: the sum over the ranks
+        assert abs(float(r["gg"][0]) - gg) <= 1e-10 * abs(gg)
+    np.testing.assert_allclose(got_y, y, rtol=1e-12, atol=1e-12)
+    for a, want in zip(got, (gb, gi, gd)):
+        np.testing.assert_allclose(a, want, rtol=1e-10, atol=1e-14)
