@@ -15,6 +15,9 @@
  *   Q_i = 10^(-bq_i/10), delta_i = 10^(-iq_i/10), zeta_i = 10^(-dq_i/10),
  *   eps = 10^(-gcp/10), beta = 1 - eps, alpha_i = 1 - (delta_i + zeta_i)
  *   (alpha_mode 1: alpha_i = 1 - 10^(-(iq_i+dq_i)/10)).
+ * With a per-base gap-continuation track gcp_i, eps_i = 10^(-gcp_i/10) and beta_i = 1 - eps_i
+ * replace eps and beta in the rows they enter (Eq. 1-3 index every transition of row i by
+ * read position i: eps_i in I(i,j) and D(i,j), beta_i in M(i,j)).
  * 'N' on either side matches every base; bases are ASCII A C G T N, either case.
  *
  * Conventions shared by every call:
@@ -42,12 +45,13 @@ extern "C" {
 #define PHMM_ENOMEM -3   /* workspace smaller than phmm_workspace_bytes() */
 #define PHMM_ECUDA -4    /* a CUDA runtime call failed; see phmm_last_cuda_error() */
 #define PHMM_ESTATE -5   /* call out of order (e.g. backward on a plan never run forward) */
+#define PHMM_EGUARD -6   /* debug builds only: a workspace guard region was overwritten, or a
+                            kernel's index check failed (the pair was flagged invalid) */
 
 #define PHMM_MAX_READ_LEN 512 /* longest read (rows) one wavefront group holds */
-/* Longest read phmm_forward scores: reads beyond PHMM_MAX_READ_LEN are swept in row tiles of
- * PHMM_MAX_READ_LEN rows (Sec. III-C supports reads up to 1,024).  phmm_backward,
- * phmm_forward_partials, phmm_grad_host and phmm_forward_noalloc take reads up to
- * PHMM_MAX_READ_LEN only. */
+/* Longest read a plan takes: reads beyond PHMM_MAX_READ_LEN are swept in row tiles of
+ * PHMM_MAX_READ_LEN rows, forward and adjoint (Sec. III-C supports reads up to 1,024).
+ * phmm_forward_noalloc takes reads up to PHMM_MAX_READ_LEN only. */
 #define PHMM_MAX_READ_LEN_FWD 2048
 
 /* ---- per-pair flags written by phmm_forward ---------------------------------------- */
@@ -82,6 +86,11 @@ typedef struct phmm_batch {
   const int32_t *pair_read;   /* [P] read index of each pair */
   const int32_t *pair_hap;    /* [P] haplotype index of each pair */
   double gcp;                 /* Phred gap-continuation penalty, > 0 */
+  const void *gcp_q;          /* [sum m] per-base gap-continuation Phred values (qual_dtype,
+                                 each > 0), or NULL: gcp at every read position.  A plan with
+                                 a track uses the extended-range FP32 first line and a fixed
+                                 read-length -> group table (the options' tables are ignored;
+                                 first_line = PHMM_FIRST_PLAIN32 is rejected with EINVAL) */
 } phmm_batch;
 
 /* First-line (bulk) arithmetic of the forward pass. */
@@ -99,7 +108,11 @@ typedef struct phmm_options {
   int32_t lanes;       /* fixed group when binning == 0: lanes per pair, 4/8/16/32 */
   int32_t rows;        /* fixed group when binning == 0: rows per lane, 4/8/12/16/20 */
   int32_t persistent;  /* 1: persistent work-queue kernels; 0: one warp group per item */
-  int32_t use_graph;   /* 1: replay the launch sequence from a captured CUDA graph */
+  int32_t use_graph;   /* 1: replay the launch sequence from a captured CUDA graph:
+                          phmm_forward always (one capture per workspace/output pointer
+                          set); phmm_forward_partials / phmm_backward_partials on batches of
+                          at most 2^30 cells, captured when a call repeats the previous
+                          call's pointers (their kernel-time events are then not recorded) */
   int32_t warps_per_block; /* 1..4 warps per block (0 = 4) */
   int32_t bin_rows[PHMM_MAX_READ_LEN / 4 + 1]; /* optional read-length -> group table */
   int32_t bin_table_valid; /* 1 if bin_rows holds a table */
@@ -147,14 +160,19 @@ int phmm_forward(phmm_plan *plan, void *ws, size_t ws_bytes, double *out_log10,
  * Adjoint: given dL[p] = d(loss)/d(log10 L_p) (device double [P]), writes
  *   d_base_q, d_ins_q, d_del_q : device float [sum m], d(loss)/d(Phred) summed over the
  *                                pairs that share each read (overwritten, FP64-accumulated);
- *   d_gcp                      : device double [1], d(loss)/d(gcp) summed over all pairs.
+ *   d_gcp_q                    : device float [sum m], the same for the per-base
+ *                                gap-continuation track (required when the batch has one,
+ *                                else ignored and may be NULL);
+ *   d_gcp                      : device double [1], d(loss)/d(gcp) summed over all pairs (with
+ *                                a track: the sum of d_gcp_q, the derivative for one shift
+ *                                of every gap-continuation value).
  * Invalid pairs contribute nothing.  Requires a preceding phmm_forward with the same plan and
- * ws (PHMM_ESTATE otherwise).  Reads longer than PHMM_MAX_READ_LEN (row tiles) have no
- * adjoint: a plan holding one returns PHMM_ETOOLONG.  Asynchronous on `stream`.
+ * ws (PHMM_ESTATE otherwise).  Reads longer than PHMM_MAX_READ_LEN are swept in the same row
+ * tiles as the forward.  Asynchronous on `stream`.
  */
 int phmm_backward(phmm_plan *plan, void *ws, size_t ws_bytes, const double *dL,
-                  float *d_base_q, float *d_ins_q, float *d_del_q, double *d_gcp,
-                  void *stream);
+                  float *d_base_q, float *d_ins_q, float *d_del_q, float *d_gcp_q,
+                  double *d_gcp, void *stream);
 
 /*
  * Fused training step, part 1: the adjoint sweep with dL = 1 for every pair.  Its own forward
@@ -164,22 +182,21 @@ int phmm_backward(phmm_plan *plan, void *ws, size_t ws_bytes, const double *dL,
  * d log10 L_p / d(Phred inputs) stays in ws.  A pair's gradient is linear in dL[p], so
  * phmm_backward_partials then only weights and reduces them: one forward sweep per step
  * instead of phmm_forward's plus the adjoint's.  Same arguments, ownership and errors as
- * phmm_forward, plus PHMM_ETOOLONG for plans holding reads longer than PHMM_MAX_READ_LEN.
- * Asynchronous on `stream`.
+ * phmm_forward.  Asynchronous on `stream`.
  */
 int phmm_forward_partials(phmm_plan *plan, void *ws, size_t ws_bytes, double *out_log10,
                           uint8_t *out_flags, void *stream);
 
 /*
- * Fused training step, part 2: writes d_base_q, d_ins_q, d_del_q and d_gcp as phmm_backward
- * does, from the partials the latest phmm_forward_partials on this plan and ws left there,
+ * Fused training step, part 2: writes d_base_q, d_ins_q, d_del_q, d_gcp_q and d_gcp as
+ * phmm_backward does, from the partials the latest phmm_forward_partials on this plan and ws left there,
  * each pair's weighted by dL[p] (device double [P]) in the FP64 per-read reduction.  May be
  * called again with another dL.  PHMM_ESTATE without a preceding phmm_forward_partials, or
  * after a phmm_backward (which overwrites the partials).  Asynchronous on `stream`.
  */
 int phmm_backward_partials(phmm_plan *plan, void *ws, size_t ws_bytes, const double *dL,
-                           float *d_base_q, float *d_ins_q, float *d_del_q, double *d_gcp,
-                           void *stream);
+                           float *d_base_q, float *d_ins_q, float *d_del_q, float *d_gcp_q,
+                           double *d_gcp, void *stream);
 
 void phmm_plan_destroy(phmm_plan *plan);
 
@@ -230,7 +247,8 @@ int phmm_plan_rescue_counts(phmm_plan *plan, const void *ws, void *stream, int64
  * tuned tables on a strided sample of the whole batch and the fastest are written.  The other
  * fields of *opt are used as given.
  *
- * The batch is validated as by phmm_plan_create (same errors).  Allocates temporary device
+ * The batch is validated as by phmm_plan_create (same errors).  A batch with a per-base
+ * gap-continuation track runs a fixed group table: nothing is tuned and *opt is unchanged.  Allocates temporary device
  * memory with cudaMallocAsync on `stream`, copies the offsets and pair lists to the host
  * and synchronises `stream` repeatedly: run it once per workload shape, before timing.
  */
@@ -264,19 +282,20 @@ void phmm_score_host_release(void);
  * subset runs the fused step (phmm_forward_partials, then phmm_backward_partials with the
  * subset's dL) and returns out_log10 / out_flags as phmm_score_host does, and
  *   d_base_q, d_ins_q, d_del_q : host float [sum m], as phmm_backward (reads without pairs: 0);
+ *   d_gcp_q                    : host float [sum m] for a batch with a per-base track (else
+ *                                ignored, may be NULL);
  *   d_gcp                      : host double [1], summed over the subsets in order.
  * A subset holds every pair of its reads, so each read's gradient comes from one subset's
  * FP64 reduction.  The first three subsets take 1/8, 1/4 and 1/2 of subset_cells and the last
  * ones halve what is left (down to 1/8), so the transfers that cannot overlap any computation
  * stay small.  The copies of one subset overlap the computation of the previous one.
- * Errors: those of phmm_score_host, PHMM_EINVAL for a NULL dL or gradient array,
- * PHMM_ETOOLONG for reads longer than PHMM_MAX_READ_LEN.  Shares phmm_score_host's buffers
- * and lock.
+ * Errors: those of phmm_score_host, PHMM_EINVAL for a NULL dL or gradient array.  Shares
+ * phmm_score_host's buffers and lock.
  */
 int phmm_grad_host(const phmm_batch *host_batch, const phmm_options *opt,
                    int64_t subset_cells, const double *dL, double *out_log10,
                    uint8_t *out_flags, float *d_base_q, float *d_ins_q, float *d_del_q,
-                   double *d_gcp);
+                   float *d_gcp_q, double *d_gcp);
 
 /*
  * Forward scoring for callers that cannot allocate device memory.
@@ -302,8 +321,9 @@ int phmm_grad_host(const phmm_batch *host_batch, const phmm_options *opt,
  * Returns PHMM_ENOMEM if the batch's scratch (16 B per read base + 1 B per read base + the
  * padded haplotype codes, about 1 B per haplotype base + 112 B per haplotype) exceeds
  * PHMM_NOALLOC_SCRATCH_BYTES, PHMM_ETOOLONG for a read longer than PHMM_MAX_READ_LEN,
- * PHMM_EINVAL for bad arguments or offsets, PHMM_ECUDA on a CUDA error.  A batch without
- * pairs returns PHMM_OK after the checks.
+ * PHMM_EINVAL for bad arguments or offsets or a batch with a per-base gap-continuation
+ * track (this entry point takes the scalar gcp only), PHMM_ECUDA on a CUDA error.  A batch
+ * without pairs returns PHMM_OK after the checks.
  *
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.  Every call
@@ -314,6 +334,22 @@ int phmm_grad_host(const phmm_batch *host_batch, const phmm_options *opt,
 #define PHMM_NOALLOC_SCRATCH_BYTES (64 << 20)
 int phmm_forward_noalloc(const phmm_batch *batch, double *out_log10, uint8_t *out_flags,
                          void *stream);
+
+/*
+ * Debug builds (libphmm_debug.so, compiled with -DPHMM_DEBUG; no counterpart in the paper):
+ * the plan's workspace holds a 256-byte guard region after every region, filled with 0xA5
+ * before each call and checked after it, and the kernels check each pair's read positions,
+ * haplotype codes, scratch slot and checkpoints against the plan's sizes, flagging the pair
+ * invalid (NaN result) instead of touching memory outside them.  phmm_forward,
+ * phmm_backward, phmm_forward_partials and phmm_backward_partials then wait for `stream`
+ * and return PHMM_EGUARD if a check failed.
+ *   phmm_debug_guard_offset: byte offset in the workspace of guard region k (PHMM_EINVAL
+ *     past the last one);
+ *   phmm_debug_check: checks the guards now (waits for `stream`).
+ * In the release library both return PHMM_ESTATE.
+ */
+int phmm_debug_guard_offset(const phmm_plan *plan, int k, size_t *offset);
+int phmm_debug_check(phmm_plan *plan, void *ws, void *stream);
 
 /*
  * Arithmetic-pipe probe (roofline denominators): lane multiply-adds per second sustained

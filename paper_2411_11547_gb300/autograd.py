@@ -1,8 +1,8 @@
 """torch.autograd.Function over the library's forward and adjoint (include/phmm.h).
 
 y_p = log10 P(read | haplotype) of every pair (Eq. 1-4 summed over the last row); the gradient
-flows to the three Phred quality tracks (float32, treated as continuous) and to the scalar
-gap-continuation Phred quality.  Both directions run in the CUDA kernels behind the C ABI; the
+flows to the three Phred quality tracks (float32, treated as continuous) and to the
+gap-continuation Phred quality: one scalar, or a per-base track of one value per read base.  Both directions run in the CUDA kernels behind the C ABI; the
 gradient sums over the pairs sharing a read are taken in FP64 on the device, deterministic.
 """
 from __future__ import annotations
@@ -15,8 +15,9 @@ from . import phmm as _ph
 class PairHMMLogLik(torch.autograd.Function):
     """log10 L for every pair; backward gives d/d(base_q, ins_q, del_q, gcp).
 
-    Arguments: float32 quality tensors `base_q, ins_q, del_q` [sum m] (device), a 0-d
-    float64/float32 tensor `gcp`, and `layout`, a dict of device tensors with keys
+    Arguments: float32 quality tensors `base_q, ins_q, del_q` [sum m] (device), `gcp` (a 0-d
+    float64/float32 tensor, or a float32 device tensor [sum m]: a per-base gap-continuation
+    track), and `layout`, a dict of device tensors with keys
     read_bases, read_off, hap_bases, hap_off, pair_read, pair_hap (and optionally
     alpha_mode).  Returns (log10L float64 [pairs], flags uint8 [pairs]); flags are not
     differentiable.  One plan (validation, binning, workspace) is built per call.  When a
@@ -27,12 +28,18 @@ class PairHMMLogLik(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, base_q, ins_q, del_q, gcp, layout, opts=None):
-        g = float(gcp.detach().reshape(()).item()) if torch.is_tensor(gcp) else float(gcp)
+        track = torch.is_tensor(gcp) and gcp.numel() > 1
+        if track:
+            g, gq = 10.0, gcp.detach().to(base_q.dtype).contiguous()
+        else:
+            g = float(gcp.detach().reshape(()).item()) if torch.is_tensor(gcp) else float(gcp)
+            gq = None
         db = _ph.DeviceBatch.from_tensors(
             layout["read_bases"], base_q.detach().contiguous(), ins_q.detach().contiguous(),
             del_q.detach().contiguous(), layout["read_off"], layout["hap_bases"],
             layout["hap_off"], layout["pair_read"], layout["pair_hap"], g,
-            layout.get("alpha_mode", 0))
+            layout.get("alpha_mode", 0), gcp_q=gq)
+        ctx.track = track
         plan = _ph.Plan(db, opts)
         ctx.fused = any(ctx.needs_input_grad[:4])
         out, flags = plan.forward_partials() if ctx.fused else plan.forward()
@@ -47,10 +54,12 @@ class PairHMMLogLik(torch.autograd.Function):
         if dy is None:
             return None, None, None, None, None, None
         dy = dy.contiguous()
-        dbq, diq, ddq, dgcp = plan.backward_partials(dy) if ctx.fused else plan.backward(dy)
+        res = plan.backward_partials(dy) if ctx.fused else plan.backward(dy)
+        dbq, diq, ddq, dgcp = res[:4]
         gg = None
         if ctx.gcp_like is not None and ctx.needs_input_grad[3]:
-            gg = dgcp.reshape(ctx.gcp_like.shape).to(ctx.gcp_like.dtype)
+            src = res[4] if ctx.track else dgcp
+            gg = src.reshape(ctx.gcp_like.shape).to(ctx.gcp_like.dtype)
         ctx.plan = None
         return dbq, diq, ddq, gg, None, None
 

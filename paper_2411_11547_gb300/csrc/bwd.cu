@@ -57,6 +57,11 @@ size_t plan_layout_bin(const phmm_plan *pl, int which);
 double plan_eps64(const phmm_plan *pl);
 int64_t plan_n_max(const phmm_plan *pl);
 int64_t plan_pair_rows(const phmm_plan *pl);
+int plan_max_m(const phmm_plan *pl);
+unsigned *plan_dbg_word(const phmm_plan *pl);
+int64_t plan_hcode_bytes(const phmm_plan *pl);
+bool plan_gq(const phmm_plan *pl);
+size_t plan_layout_rgap(const phmm_plan *pl);
 const int *plan_bwd_cfg_of_m(const phmm_plan *pl);
 const std::vector<int> &plan_bwd_used(const phmm_plan *pl);
 
@@ -65,14 +70,15 @@ int launch_binning(const phmm_batch &b, const CfgTable &tab, int32_t *key, int32
                    int32_t *order, cudaStream_t s, int *launches);
 int pair_offsets(const phmm_batch &b, char *scratch, int64_t **poff, cudaStream_t s);
 int reduce_gradients(const phmm_batch &b, char *scratch, const float *part_bq,
-                     const float *part_iq, const float *part_dq, const double *pair_dgcp,
-                     const double *dL, float *dbq, float *diq, float *ddq, double *dgcp,
-                     cudaStream_t s, int *launches);
+                     const float *part_iq, const float *part_dq, const float *part_gq,
+                     const double *pair_dgcp, const double *dL, float *dbq, float *diq,
+                     float *ddq, float *dgq, double *dgcp, cudaStream_t s, int *launches);
 size_t reduce_scratch_bytes_aligned(int64_t P, int64_t R);
 
 // ------------------------------------------------------------------------ host side ------
 
-static BwdKernel bwd_kernel32(int L, int K) {
+static BwdKernel bwd_kernel32(int L, int K, bool gq = false) {
+  if (gq) return bwd32_gq(L, K);
   switch (L) {
     case 4:
     case 8: return bwd32_lo(L, K);
@@ -81,7 +87,9 @@ static BwdKernel bwd_kernel32(int L, int K) {
     default: return nullptr;
   }
 }
-static BwdKernel bwd_kernel64(int K) { return bwd64_table(K); }
+static BwdKernel bwd_kernel64(int K, bool gq = false) {
+  return gq ? bwd64_gq(K) : bwd64_table(K);
+}
 
 // 1 if the FP32 adjoint is built for group `cfg`.
 int bwd_cfg_supported(int cfg) {
@@ -126,13 +134,32 @@ static int64_t bwd_nchk(int L, int K, int elem, int64_t n_max) {
   return ramp + (steps + seg - 1) / seg + 2;
 }
 
-static int64_t slot_elems(int L, int K, int elem, int64_t n_max) {
-  return bwd_nchk(L, K, elem, n_max) * 32 * ck_w(K, elem);
+// Row tiles a slot of group (L, K) holds for a plan whose longest read is max_m: reads longer
+// than one group are swept in tiles of 512 rows by the 32 x 16 group only.
+static int ntile_cap(int L, int K, int max_m) {
+  if (L != 32 || K != 16 || max_m <= 32 * 16) return 1;
+  return (max_m + 32 * 16 - 1) / (32 * 16);
+}
+
+// A slot (elements of the kernel's type): the checkpoints of every row tile, then for tiled
+// plans the last row of every tile but the last and two buffers of a tile's first-row
+// adjoints, each n_max columns of 4 values.
+static int64_t slot_elems(int L, int K, int elem, int64_t n_max, int ntile) {
+  int64_t e = (int64_t)ntile * bwd_nchk(L, K, elem, n_max) * 32 * ck_w(K, elem);
+  if (ntile > 1) e += (int64_t)(ntile - 1 + 2) * n_max * 4;
+  return e;
 }
 
 struct BwdLayout {
-  size_t part, pdgcp, red, slots, total;
+  size_t part, pdgcp, red, slots, slots_bytes, total;
+  std::vector<size_t> guards;  // debug builds: a guard region after every region
 };
+
+#ifdef PHMM_DEBUG
+constexpr bool kDebugB = true;
+#else
+constexpr bool kDebugB = false;
+#endif
 
 static BwdLayout bwd_layout(const phmm_plan *pl) {
   const phmm_batch &b = plan_batch(pl);
@@ -142,10 +169,14 @@ static BwdLayout bwd_layout(const phmm_plan *pl) {
   auto take = [&](size_t bytes) {
     size_t at = o;
     o = (o + bytes + 255) & ~(size_t)255;
+    if (kDebugB) {
+      Lo.guards.push_back(o);
+      o += 256;
+    }
     return at;
   };
   const int64_t rows = plan_pair_rows(pl) + 1;
-  Lo.part = take(3 * 4 * (size_t)rows);
+  Lo.part = take((plan_gq(pl) ? 4 : 3) * 4 * (size_t)rows);
   Lo.pdgcp = take(8 * (size_t)(b.n_pairs + 1));
   Lo.red = take(reduce_scratch_bytes_aligned(b.n_pairs, b.n_reads));
   size_t slots = 0;
@@ -154,24 +185,30 @@ static BwdLayout bwd_layout(const phmm_plan *pl) {
     const int L = cfg_lanes(cfg), K = cfg_rows(cfg);
     const int block = bwd_block(K, 4, wpb);
     const size_t nslot = (size_t)plan_sms(pl) *
-                         blocks_per_sm(bwd_kernel32(L, K), bwd_smem(K, 4, block), block) *
+                         blocks_per_sm(bwd_kernel32(L, K, plan_gq(pl)), bwd_smem(K, 4, block),
+                                       block) *
                          (block / 32);
-    slots = std::max(slots, nslot * 4 * (size_t)slot_elems(L, K, 4, nmax));
+    slots = std::max(slots, nslot * 4 * (size_t)slot_elems(L, K, 4, nmax,
+                                                             ntile_cap(L, K, plan_max_m(pl))));
   }
   for (int c = 0; c < kNumCfg64; ++c) {
     const int K = rows64(c);
     const int block = bwd_block(K, 8, wpb);
     const size_t nslot = (size_t)plan_sms(pl) *
-                         blocks_per_sm(bwd_kernel64(K), bwd_smem(K, 8, block), block) *
+                         blocks_per_sm(bwd_kernel64(K, plan_gq(pl)), bwd_smem(K, 8, block),
+                                       block) *
                          (block / 32);
-    slots = std::max(slots, nslot * 8 * (size_t)slot_elems(32, K, 8, nmax));
+    slots = std::max(slots, nslot * 8 * (size_t)slot_elems(32, K, 8, nmax,
+                                                             ntile_cap(32, K, plan_max_m(pl))));
   }
   Lo.slots = take(slots);
+  Lo.slots_bytes = slots;
   Lo.total = o;
   return Lo;
 }
 
 size_t bwd_workspace_bytes(const phmm_plan *pl) { return bwd_layout(pl).total; }
+std::vector<size_t> bwd_guard_offsets(const phmm_plan *pl) { return bwd_layout(pl).guards; }
 
 #define CKB(x)                          \
   do {                                  \
@@ -192,6 +229,7 @@ int bwd_sweep_impl(phmm_plan *pl, char *ws, const double *dL, double *out, uint8
   float *part = (float *)(bw + Lo.part);
   const int64_t rows = plan_pair_rows(pl) + 1;
   float *part_bq = part, *part_iq = part + rows, *part_dq = part + 2 * rows;
+  float *part_gq = plan_gq(pl) ? part + 3 * rows : nullptr;
   double *pdg = (double *)(bw + Lo.pdgcp);
   char *red = bw + Lo.red;
   int64_t *poff = nullptr;
@@ -224,6 +262,8 @@ int bwd_sweep_impl(phmm_plan *pl, char *ws, const double *dL, double *out, uint8
     f.bq = b.base_q;
     f.iq = b.ins_q;
     f.dq = b.del_q;
+    f.gq = b.gcp_q;
+    f.rgap = plan_gq(pl) ? (const float2 *)(ws + plan_layout_rgap(pl)) : nullptr;
     f.qual_f32 = b.qual_dtype == PHMM_QUAL_F32;
     f.alpha_mode = b.alpha_mode;
     f.n_reads = b.n_reads;
@@ -234,6 +274,9 @@ int bwd_sweep_impl(phmm_plan *pl, char *ws, const double *dL, double *out, uint8
     f.eps64 = eps64;
     f.beta64 = 1.0 - eps64;
     f.persistent = 1;
+    f.dbg_err = plan_dbg_word(pl);  // debug builds only (else null: no checks)
+    f.dbg_sum_m = plan_sum_m(pl);
+    f.dbg_hcode_bytes = plan_hcode_bytes(pl);
     a.dL = dL;
     a.out = out;
     a.oflags = oflags;
@@ -241,6 +284,7 @@ int bwd_sweep_impl(phmm_plan *pl, char *ws, const double *dL, double *out, uint8
     a.part_bq = part_bq;
     a.part_iq = part_iq;
     a.part_dq = part_dq;
+    a.part_gq = part_gq;
     a.pair_dgcp = pdg;
     a.scratch = bw + Lo.slots;
     int32_t *rlist = (int32_t *)(ws + plan_layout_bin(pl, 8));
@@ -261,14 +305,18 @@ int bwd_sweep_impl(phmm_plan *pl, char *ws, const double *dL, double *out, uint8
       c.f.count_dev = grp_count + cfg;
       c.f.counter = (int32_t *)(ws + plan_layout_bin(pl, 7)) + cfg;
       c.nchk = (int32_t)bwd_nchk(L, K, 4, nmax);
-      c.slot_elems = slot_elems(L, K, 4, nmax);
+      c.ntile_cap = ntile_cap(L, K, plan_max_m(pl));
+      c.ck_tile = (int64_t)c.nchk * 32 * ck_w(K, 4);
+      c.tile_cols = nmax;
+      c.slot_elems = slot_elems(L, K, 4, nmax, c.ntile_cap);
       c.rescue = o.adjoint_rescue ? 0 : 1;  // without the FP64 pass, failures write NaN
       c.all64 = o.adjoint_rescue == 2 ? 1 : 0;
-      BwdKernel k = bwd_kernel32(L, K);
+      BwdKernel k = bwd_kernel32(L, K, plan_gq(pl));
       if (!k) return (int)cudaErrorInvalidValue;
       const int block = bwd_block(K, 4, o.bwd_warps_per_block);
       const size_t sm = bwd_smem(K, 4, block);
       const int grid = plan_sms(pl) * blocks_per_sm(k, sm, block);
+      c.f.dbg_nslots = (int64_t)(Lo.slots_bytes / (4 * (size_t)c.slot_elems));
       k<<<grid, block, sm, s>>>(c);
       CKB(cudaGetLastError());
       ++*launches;
@@ -282,12 +330,16 @@ int bwd_sweep_impl(phmm_plan *pl, char *ws, const double *dL, double *out, uint8
       c.f.count_dev = rcnt + k64;
       c.f.counter = rctr + k64;
       c.nchk = (int32_t)bwd_nchk(32, K, 8, nmax);
-      c.slot_elems = slot_elems(32, K, 8, nmax);
+      c.ntile_cap = ntile_cap(32, K, plan_max_m(pl));
+      c.ck_tile = (int64_t)c.nchk * 32 * ck_w(K, 8);
+      c.tile_cols = nmax;
+      c.slot_elems = slot_elems(32, K, 8, nmax, c.ntile_cap);
       c.rescue = 1;
-      BwdKernel kk = bwd_kernel64(K);
+      BwdKernel kk = bwd_kernel64(K, plan_gq(pl));
       const int block = bwd_block(K, 8, o.bwd_warps_per_block);
       const size_t sm = bwd_smem(K, 8, block);
       const int grid = plan_sms(pl) * blocks_per_sm(kk, sm, block);
+      c.f.dbg_nslots = (int64_t)(Lo.slots_bytes / (8 * (size_t)c.slot_elems));
       kk<<<grid, block, sm, s>>>(c);
       CKB(cudaGetLastError());
       ++*launches;
@@ -302,14 +354,17 @@ int bwd_sweep_impl(phmm_plan *pl, char *ws, const double *dL, double *out, uint8
 // The per-read FP64 reduction of the partials the latest sweep left in the workspace, each
 // pair's weighted by dL[p] when given.  ev1: event recorded after it.
 int bwd_reduce_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, float *diq,
-                    float *ddq, double *dgcp, cudaStream_t s, int *launches, cudaEvent_t ev1) {
+                    float *ddq, float *dgq, double *dgcp, cudaStream_t s, int *launches,
+                    cudaEvent_t ev1) {
   const phmm_batch &b = plan_batch(pl);
   const BwdLayout Lo = bwd_layout(pl);
   char *bw = ws + plan_bwd_offset(pl);
   float *part = (float *)(bw + Lo.part);
   const int64_t rows = plan_pair_rows(pl) + 1;
+  const bool gq = plan_gq(pl) && dgq;
   CKB(reduce_gradients(b, bw + Lo.red, part, part + rows, part + 2 * rows,
-                       (const double *)(bw + Lo.pdgcp), dL, dbq, diq, ddq, dgcp, s, launches));
+                       gq ? part + 3 * rows : nullptr, (const double *)(bw + Lo.pdgcp), dL, dbq,
+                       diq, ddq, gq ? dgq : nullptr, dgcp, s, launches));
   CKB(cudaEventRecord(ev1, s));
   return 0;
 }
@@ -317,10 +372,10 @@ int bwd_reduce_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, float
 // The whole backward: sweep with the partials scaled by dL, then the reduction.
 // ev3: events recorded before the adjoint kernels, after them, and after the reduction.
 int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, float *diq,
-                     float *ddq, double *dgcp, cudaStream_t s, int *launches,
+                     float *ddq, float *dgq, double *dgcp, cudaStream_t s, int *launches,
                      cudaEvent_t *ev3) {
   CKB(bwd_sweep_impl(pl, ws, dL, nullptr, nullptr, s, launches, ev3));
-  return bwd_reduce_impl(pl, ws, nullptr, dbq, diq, ddq, dgcp, s, launches, ev3[2]);
+  return bwd_reduce_impl(pl, ws, nullptr, dbq, diq, ddq, dgq, dgcp, s, launches, ev3[2]);
 }
 
 }  // namespace phmm

@@ -16,10 +16,14 @@ struct BwdArgs {
   uint8_t *oflags;         //   own forward pass (the fused forward-with-partials call)
   const int64_t *poff;     // partial-gradient offsets per pair
   float *part_bq, *part_iq, *part_dq;
+  float *part_gq;          // per-base gap-continuation partials (plans with a track)
   double *pair_dgcp;
   void *scratch;           // per-warp slots (elements of the kernel's type)
   int64_t slot_elems;
-  int32_t nchk;            // checkpoint capacity per slot
+  int32_t nchk;            // checkpoint capacity per slot and row tile
+  int64_t ck_tile;         // elements of one row tile's checkpoints in a slot (nchk x 32 x width)
+  int32_t ntile_cap;       // row tiles a slot holds (reads longer than one group: 32 x 16 only)
+  int64_t tile_cols;       // columns of the row-tile buffers (the longest haplotype)
   int32_t rescue;          // 1: this is the FP64 pass (write NaN on failure)
   int32_t all64;           // FP32 pass: hand every valid pair to the FP64 pass untouched
   int32_t *resc_list[kNumCfg64];  // FP32 pass: pairs handed to the FP64 pass
@@ -149,9 +153,12 @@ struct AdjState {
 // keep: the lane prefers the exponent Ek (which keeps its posterior scale, and so the scale
 // of its partial sums, unchanged) whenever that leaves its largest adjoint within 2^+-24;
 // otherwise it normalises the largest to [1, 2).
+// ovr: the last lane of a row tile above another takes the lane below's exponent and size
+// from (Eo, xo), the tile below's first-row adjoints about to arrive, for its adoption.
 template <typename T, int L, int K, int kBias>
 __device__ __forceinline__ void adj_rescale(AdjState<T, K> &as, int t, T S, int ES,
-                                            bool apply = true, bool keep = false, int Ek = 0) {
+                                            bool apply = true, bool keep = false, int Ek = 0,
+                                            bool ovr = false, int Eo = 0, T xo = 0) {
   constexpr unsigned FULL = 0xffffffffu;
   T mx = fmax(as.Itop, fabs(as.diagU));
 #pragma unroll
@@ -172,9 +179,14 @@ __device__ __forceinline__ void adj_rescale(AdjState<T, K> &as, int t, T S, int 
     as.EB = En;
   }
   const T xb = fmax(fabs(as.u[0]), as.Itop);
-  const int Elow = __shfl_down_sync(FULL, as.EB, 1, L);
-  const T xbl = __shfl_down_sync(FULL, xb, 1, L);
-  if (apply && zero && t < L - 1)
+  int Elow = __shfl_down_sync(FULL, as.EB, 1, L);
+  T xbl = __shfl_down_sync(FULL, xb, 1, L);
+  const bool last_ovr = ovr && t == L - 1;
+  if (last_ovr) {
+    Elow = Eo;
+    xbl = xo;
+  }
+  if (apply && zero && (t < L - 1 || last_ovr))
     as.EB = Elow - kBias * (K - 1) + (xbl > (T)0 ? Num<T>::ilog2(xbl) : 0);
   as.fB = t < L - 1 ? Num<T>::exp2i(Elow - as.EB - kBias * (K - 1)) : (T)0;
   as.seed = (t == L - 1 && S > (T)0) ? Num<T>::exp2i(-ES - as.EB) / S : (T)0;
@@ -187,7 +199,9 @@ constexpr int bwd_min_blocks() {
   return sizeof(T) == 8 ? 1 : (K <= 4 ? 4 : (K <= 6 ? 3 : 2));
 }
 
-template <typename T, int L, int K>
+// GQ: the batch has a per-base gap-continuation track: row r takes eps_r and beta_r, and the
+// gap-continuation partials are kept per row (three more sums per row) for d/dgcp_r.
+template <typename T, int L, int K, bool GQ = false>
 __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const BwdArgs a) {
   using G_ = TableGeom<T, K>;
   constexpr int G = 32 / L, VW = G_::VW, LS = G_::LS, CS = G_::CS;
@@ -202,6 +216,14 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
   constexpr int kHmin = sizeof(T) == 4 ? -100 : -900;
   constexpr int kNoScale = -(1 << 30);
   constexpr unsigned FULL = 0xffffffffu;
+  // Row tiles (Sec. III-C handles reads up to 1,024 bases): the 32 x 16 group sweeps reads
+  // longer than its 512 rows in tiles of 512 rows, as the forward does.  One pair per warp,
+  // so every tile loop is warp-uniform.  Phase A runs the tiles top to bottom, each tile's
+  // last lane handing its last row (per column) to the next tile's lane 0; phase B runs them
+  // bottom to top, each tile's lane 0 handing its first row's adjoints (per column) to the
+  // tile above's last lane, which also forms the partials that pair the two rows.
+  constexpr bool TILED = L == 32 && K == 16;
+  constexpr int LK = L * K;
   const FwdArgs &fa = a.f;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -215,12 +237,27 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
   const int wpb = blockDim.x >> 5;
   T *slot = reinterpret_cast<T *>(a.scratch) + (size_t)(blockIdx.x * wpb + warp) * a.slot_elems;
   T *ckb = slot;
+  // after the tiles' checkpoints: the last row of every tile but the last (forward values
+  // and the last lane's exponent, per column) and two alternating buffers of a tile's first
+  // row adjoints (u, I^ and lane 0's exponent, per column)
+  TileCol<T> *fbuf = nullptr, *abuf = nullptr;
+  if constexpr (TILED) {
+    fbuf = reinterpret_cast<TileCol<T> *>(slot + (size_t)a.ntile_cap * a.ck_tile);
+    abuf = fbuf + (size_t)(a.ntile_cap - 1) * a.tile_cols;
+  }
   const T eps = sizeof(T) == 4 ? (T)fa.eps32 : (T)fa.eps64;
   const T beta = sizeof(T) == 4 ? (T)fa.beta32 : (T)fa.beta64;
 
   const int64_t count = *fa.count_dev;
   const int64_t base = fa.offset_dev ? *fa.offset_dev : 0;
   const int64_t nitems = (count + G - 1) / G;
+#ifdef PHMM_DEBUG
+  // the warp's scratch slot inside the workspace's slot region
+  if (fa.dbg_err && (int64_t)blockIdx.x * wpb + warp >= fa.dbg_nslots) {
+    if (lane == 0) atomicOr(fa.dbg_err, kDbgSlot);
+    return;
+  }
+#endif
 
   for (;;) {
     int it = 0;
@@ -243,7 +280,22 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
         m = (int)(fa.read_off[ri + 1] - r0);
         hs = hap_start(fa.hap_off[hi], hi);
         n = fa.hap_off[hi + 1] - fa.hap_off[hi];
-        if (m <= 0 || m > L * K || n <= 0) bad = true;
+        const int cap = TILED ? LK * a.ntile_cap : LK;
+        if (m <= 0 || m > cap || n <= 0 || (TILED && m > LK && n > a.tile_cols)) bad = true;
+#ifdef PHMM_DEBUG
+        // the pair's read positions and haplotype codes (with their guards) inside the
+        // buffers, and its columns inside the row-tile buffers (sized by the longest one)
+        if (!bad && fa.dbg_err &&
+            (r0 + m > fa.dbg_sum_m || hs < kHapGuard ||
+             hs + ((n + 15) & ~(int64_t)15) + kHapGuard > fa.dbg_hcode_bytes)) {
+          atomicOr(fa.dbg_err, kDbgPairIndex);
+          bad = true;
+        }
+        if (!bad && fa.dbg_err && n > a.tile_cols) {
+          atomicOr(fa.dbg_err, kDbgCheckpoints);
+          bad = true;
+        }
+#endif
       } else {
         bad = true;
       }
@@ -259,86 +311,76 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
       }
       continue;
     }
-    const int npad = L * K - m;
-    // pad rows: the rows above row 1 (their partials are never used)
-    const int first = npad - t * K;          // local index of the lane's first real row
-    // lanes whose products can matter: those holding a real row, and the pad lane just above
-    // a first real row that starts a lane (its last row's S feeds that row's beta partial)
-    const bool real_lane = first <= K;
+    const int ntile = (TILED && m > LK) ? (m + LK - 1) / LK : 1;
+    const int npad = ntile * LK - m;  // pad rows above row 1, all in the first tile
     const T bnd = n > 0 ? (T)1 / (T)n : (T)0;
     T ap[K], dl[K], zt[K], ei[K];
+    T er[GQ ? K : 1];  // per-row gap continuation (track only)
     WfState<T, K> st;
+    // per-row constants and the emission table of one tile's rows; the lane's rows start at
+    // zero, pad rows carrying the row-0 boundary down in I
+    auto setup_tile = [&](int tile) {
 #pragma unroll
-    for (int rv = 0; rv < K; rv += VW) {
-      T ev[kCodes][VW];
+      for (int rv = 0; rv < K; rv += VW) {
+        T ev[kCodes][VW];
 #pragma unroll
-      for (int u = 0; u < VW; ++u) {
-        const int rr = rv + u;
-        if (rr >= K) {  // table padding past the lane's rows
+        for (int u = 0; u < VW; ++u) {
+          const int rr = rv + u;
+          if (rr >= K) {  // table padding past the lane's rows
 #pragma unroll
-          for (int c = 0; c < kCodes; ++c) ev[c][u] = 0;
-          continue;
-        }
-        const int pos = t * K + rr - npad;
-        const T bias = rr ? (T)(1 << kBias) : (T)1;
-        st.M[rr] = 0;
-        st.D[rr] = 0;
-        if (pos >= 0) {
-          T Q;
-          row_params<T>(fa, r0 + pos, ap[rr], dl[rr], zt[rr], Q);
-          const int code = fa.rcode[r0 + pos];
-          ei[rr] = pos == 0 ? (T)0 : eps * bias;
-          dl[rr] *= bias;
-          st.I[rr] = 0;
-          const T em = bias * (beta * ((T)1 - Q)), ex = bias * (beta * (Q / (T)3));
-#pragma unroll
-          for (int c = 0; c < kNull; ++c) {
-            const bool mt = c == code || c == kN || code == kN;
-            ev[c][u] = mt ? em : -ex;
+            for (int c = 0; c < kCodes; ++c) ev[c][u] = 0;
+            continue;
           }
-          ev[kNull][u] = 0;
-        } else {
-          ap[rr] = 0;
-          dl[rr] = 0;
-          zt[rr] = 0;
-          ei[rr] = bias;
-          st.I[rr] = bnd * (T)(1ll << (kBias * rr));
+          const int pos = tile * LK + t * K + rr - npad;
+          const T bias = rr ? (T)(1 << kBias) : (T)1;
+          st.M[rr] = 0;
+          st.D[rr] = 0;
+          T epr = eps, ber = beta;
+          if constexpr (GQ) {
+            if (pos >= 0) row_gap<T>(fa, r0 + pos, epr, ber);
+            er[rr] = epr;
+          }
+          if (pos >= 0) {
+            T Q;
+            row_params<T>(fa, r0 + pos, ap[rr], dl[rr], zt[rr], Q, GQ ? (double)ber : 0.0);
+            const int code = fa.rcode[r0 + pos];
+            ei[rr] = pos == 0 ? (T)0 : epr * bias;
+            dl[rr] *= bias;
+            st.I[rr] = 0;
+            const T em = bias * (ber * ((T)1 - Q)), ex = bias * (ber * (Q / (T)3));
 #pragma unroll
-          for (int c = 0; c < kCodes; ++c) ev[c][u] = 0;
+            for (int c = 0; c < kNull; ++c) {
+              const bool mt = c == code || c == kN || code == kN;
+              ev[c][u] = mt ? em : -ex;
+            }
+            ev[kNull][u] = 0;
+          } else {
+            ap[rr] = 0;
+            dl[rr] = 0;
+            zt[rr] = 0;
+            ei[rr] = bias;
+            st.I[rr] = bnd * (T)(1ll << (kBias * rr));
+#pragma unroll
+            for (int c = 0; c < kCodes; ++c) ev[c][u] = 0;
+          }
         }
-      }
 #pragma unroll
-      for (int c = 0; c < kCodes; ++c) store_vec<T, VW>(tblE + c * CS + rv, ev[c]);
-    }
-    // Coefficients of the row just below the strip (the lower lane's row 0, unbiased)
-    const T apb = __shfl_down_sync(FULL, ap[0], 1, L);
-    const T dlb = __shfl_down_sync(FULL, dl[0], 1, L);
-    const T eib = __shfl_down_sync(FULL, ei[0], 1, L);
+        for (int c = 0; c < kCodes; ++c) store_vec<T, VW>(tblE + c * CS + rv, ev[c]);
+      }
+    };
 
-    // ---- phase A: forward with checkpoints -------------------------------------------------
     int steps = n > 0 ? (int)n + L - 1 : 0;
     steps = __reduce_max_sync(FULL, steps);
     const int ramp = steps < ((L + 15) & ~15) ? steps : ((L + 15) & ~15);
     const int nq = ramp + (steps - ramp + kSeg - 1) / kSeg;
-    st.c = kNull;
-    st.Md = 0;
-    st.Sd = t == 0 ? bnd : (T)0;
-    st.acc = 0;
-    st.f = t == 0 ? (T)1 : Num<T>::exp2i(-kBias * (K - 1));
-    st.E = 0;
     const int fin = n > 0 ? (int)n + L - 1 : 0;
-    T Sfin = 0;
-    int Efin = 0;
-    bool done = false;
-    // whether the lane's forward state is nonzero at the current checkpoint (kept with the
-    // checkpoint's exponent, so the reverse knows which segments hold forward values)
-    bool nzA;
-    {
-      T mx = fmax(st.Md, st.Sd);
-#pragma unroll
-      for (int r = 0; r < K; ++r) mx = fmax(mx, st.I[r]);  // M and D start at zero
-      nzA = mx > (T)0;
+#ifdef PHMM_DEBUG
+    // every checkpoint of the warp's longest pair inside the slot (warp-uniform)
+    if (fa.dbg_err && nq > a.nchk) {
+      if (lane == 0) atomicOr(fa.dbg_err, kDbgCheckpoints);
+      continue;
     }
+#endif
     // Haplotype codes of the lane's columns over segment qq's steps, one byte per step (at
     // step s lane t is at column s + 1 - t; columns outside 1..n take the null code).  Every
     // lane reads its own 8-byte window, one segment ahead: no code exchange and no load on
@@ -360,368 +402,605 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
       return ((uint64_t)hi << 32) | lo;
     };
     auto code_at = [](uint64_t cs, int u) { return (int)((cs >> (8 * u)) & 0xff); };
-    uint64_t segc = seg_codes(0);
-    for (int q = 0; q < nq; ++q) {
-      const int b = q < ramp ? q : ramp + kSeg * (q - ramp);
-      const int len = q < ramp ? 1 : kSeg;
-      const uint64_t cur = segc;
-      segc = seg_codes(q + 1);
-      {
-        T ck[CKW];
-#pragma unroll
-        for (int r = 0; r < K; ++r) {
-          ck[r] = st.M[r];
-          ck[K + r] = st.I[r];
-          ck[2 * K + r] = st.D[r];
+    // the row above a lower tile, at the columns of the steps b .. b + kSeg - 1 of lane 0
+    // (lane u holds column b + u + 1), read once per segment
+    auto load_above = [&](const TileCol<T> *above, int b) {
+      TileCol<T> cb = {0, 0, 0, 0};
+      const int64_t c = (int64_t)b + lane;
+      if (above && lane < kSeg && c < n) cb = above[c];
+      return cb;
+    };
+    // one forward step (phase A or the recompute): lane 0 takes the row above its strip from
+    // the row-0 boundary (first tile) or from the tile above (its u-th column in cb)
+    auto fstep = [&](int code, int u, const TileCol<T> &cb, bool above) {
+      T in3[3];
+      if constexpr (TILED) {
+        T tM = 0, tI = bnd * st.f, tT = bnd * st.f;  // K0 D(0, j), in lane 0's scale
+        if (above) {  // warp-uniform (one pair per warp)
+          const T bM = __shfl_sync(FULL, cb.M, u), bI = __shfl_sync(FULL, cb.I, u);
+          const T bX = __shfl_sync(FULL, cb.X, u), bE = __shfl_sync(FULL, cb.E, u);
+          const T cv = Num<T>::exp2i((int)bE - st.E - kBias * (K - 1));
+          tM = bM * cv;
+          tI = bI * cv;
+          tT = bX * cv;
         }
-        ck[3 * K] = st.Md;
-        ck[3 * K + 1] = st.Sd;
-        ck[3 * K + 2] = st.f;
-        ck[3 * K + 3] = int_bits<T>(2 * st.E + (nzA ? 1 : 0));
+        wf_step<T, L, K, true, true, true, true, true, GQ>(st, code, t, bnd, eps, tblE, ap, dl,
+                                                           zt, ei, in3, tM, tI, tT, er);
+      } else {
+        wf_step<T, L, K, true, true, true, false, true, GQ>(st, code, t, bnd, eps, tblE, ap, dl,
+                                                            zt, ei, in3, 0, 0, 0, er);
+      }
+    };
+
+    // ---- phase A: forward with checkpoints, tile by tile from the top ---------------------
+    T Sfin = 0;
+    int Efin = 0;
+    uint32_t nz_end = 0;  // bit per tile: the lane's state is nonzero after its last segment
+    for (int tile = 0; tile < ntile; ++tile) {
+      const bool last_tile = tile == ntile - 1;
+      if constexpr (TILED) __syncwarp();  // the tile above's last row is in memory
+      setup_tile(tile);
+      T *ckt = ckb + (size_t)tile * a.ck_tile;
+      const TileCol<T> *above = nullptr;
+      TileCol<T> *below_out = nullptr;
+      if constexpr (TILED) {
+        if (tile > 0) above = fbuf + (size_t)(tile - 1) * a.tile_cols;
+        if (!last_tile) below_out = fbuf + (size_t)tile * a.tile_cols;
+      }
+      st.c = kNull;
+      st.Md = 0;
+      st.Sd = (t == 0 && tile == 0) ? bnd : (T)0;
+      st.acc = 0;
+      st.f = t == 0 ? (T)1 : Num<T>::exp2i(-kBias * (K - 1));
+      st.E = 0;
+      if constexpr (TILED) {
+        // lane 0 of a lower tile starts at the exponent that brings column 1 of the row above
+        // near 1 (its own state is still zero, so this changes nothing else)
+        if (above && t == 0) {
+          const TileCol<T> c1 = above[0];
+          const T mx = fmax(c1.M, fmax(c1.I, c1.X));
+          st.E = mx > (T)0 ? (int)c1.E - kBias * (K - 1) + Num<T>::ilog2(mx) : 0;
+          st.f = Num<T>::exp2i(-st.E);
+        }
+      }
+      bool done = false;
+      // whether the lane's forward state is nonzero at the current checkpoint (kept with the
+      // checkpoint's exponent, so the reverse knows which segments hold forward values)
+      bool nzA;
+      {
+        T mx = fmax(st.Md, st.Sd);
 #pragma unroll
-        for (int k = 3 * K + 4; k < CKW; ++k) ck[k] = 0;
-        rec_store<T, CKW, true>(ckb + (size_t)q * 32 * CKW, lane, ck);
+        for (int r = 0; r < K; ++r) mx = fmax(mx, st.I[r]);  // M and D start at zero
+        nzA = mx > (T)0;
       }
-      for (int u = 0; u < len; ++u) {
-        T in3[3];
-        wf_step<T, L, K, true, true, true, false, true>(st, code_at(cur, u), t, bnd, eps, tblE,
-                                                        ap, dl, zt, ei, in3);
+      uint64_t segc = seg_codes(0);
+      for (int q = 0; q < nq; ++q) {
+        const int b = q < ramp ? q : ramp + kSeg * (q - ramp);
+        const int len = q < ramp ? 1 : kSeg;
+        const uint64_t cur = segc;
+        segc = seg_codes(q + 1);
+        {
+          T ck[CKW];
+#pragma unroll
+          for (int r = 0; r < K; ++r) {
+            ck[r] = st.M[r];
+            ck[K + r] = st.I[r];
+            ck[2 * K + r] = st.D[r];
+          }
+          ck[3 * K] = st.Md;
+          ck[3 * K + 1] = st.Sd;
+          ck[3 * K + 2] = st.f;
+          ck[3 * K + 3] = int_bits<T>(2 * st.E + (nzA ? 1 : 0));
+#pragma unroll
+          for (int k = 3 * K + 4; k < CKW; ++k) ck[k] = 0;
+          rec_store<T, CKW, true>(ckt + (size_t)q * 32 * CKW, lane, ck);
+        }
+        TileCol<T> cb = {0, 0, 0, 0};
+        if constexpr (TILED) cb = load_above(above, b);
+        for (int u = 0; u < len; ++u) {
+          fstep(code_at(cur, u), u, cb, above != nullptr);
+          if constexpr (TILED) {
+            // the tile's last row, column by column, for the tile below
+            const int64_t j = (int64_t)b + u + 1 - (L - 1);  // the last lane's column
+            if (below_out && t == L - 1 && j >= 1 && j <= n) {
+              TileCol<T> o;
+              o.M = st.M[K - 1];
+              o.I = st.I[K - 1];
+              o.X = st.I[K - 1] + zt[K - 1] * st.D[K - 1];
+              o.E = (T)st.E;
+              below_out[j - 1] = o;
+            }
+          }
+        }
+        if (last_tile && !done && b + len >= fin) {
+          Sfin = st.acc;
+          Efin = st.E;
+          done = true;
+        }
+        nzA = wf_rescale<T, L, K, kBias>(st, t);
       }
-      if (!done && b + len >= fin) {
+      if (last_tile && !done) {
         Sfin = st.acc;
         Efin = st.E;
-        done = true;
       }
-      nzA = wf_rescale<T, L, K, kBias>(st, t);
+      if (nzA) nz_end |= 1u << tile;
     }
-    if (!done) {
-      Sfin = st.acc;
-      Efin = st.E;
-    }
-    // L = S * 2^(ES - kBias (K-1)), held by the last lane of the group
+    // L = S * 2^(ES - kBias (K-1)), held by the last lane of the group (last tile)
     const T S = __shfl_sync(FULL, Sfin, sub * L + L - 1);
     const int ES = __shfl_sync(FULL, Efin, sub * L + L - 1);
     const bool okS = S > (T)0 && S < (sizeof(T) == 4 ? (T)3.0e38f : (T)1.7e308);
     bool hard = !okS;
 
-    // ---- phase B: adjoint, segment by segment from the right ------------------------------
-    AdjState<T, K> as;
-#pragma unroll
-    for (int r = 0; r < K; ++r) as.u[r] = as.Db[r] = 0;
-    as.Itop = as.diagU = 0;
-    as.EB = t == L - 1 ? -ES : 0;
-    as.fB = 0;
-    as.seed = 0;
-    as.nz = false;
-    adj_rescale<T, L, K, kBias>(as, t, okS ? S : (T)0, ES);
-    // Partial sums, each held as (true value) x 2^-H, the lane's accumulator scale.
-    // Per row r: gA (alpha_r: u(r,j+1) M(r-1,j)), gD (delta_r: I^(r,j) M(r-1,j)),
-    // gZ (zeta_r: D^(r,j+1) M(r,j)), gY (M^(r,j) M(r,j)), gX (its mismatch-column part
-    // times -e_mismatch).  gAl / gDl: the products for the lower lane's row 0.
-    // Lane scalars: gS (beta: u S of the row above), gEI (eps via I), gED (eps via D).
-    T gA[K], gD[K], gZ[K], gY[K], gX[K];
-#pragma unroll
-    for (int r = 0; r < K; ++r) gA[r] = gD[r] = gZ[r] = gY[r] = gX[r] = 0;
-    T gAl = 0, gDl = 0, gS = 0, gEI = 0, gED = 0;
-    int H = kNoScale;
+    // ---- phase B: adjoint, tile by tile from the bottom, segment by segment from the right
+    const double dy = (valid && !bad && a.dL) ? a.dL[p] : 1.0;
+    const int64_t po = (valid && !bad) ? a.poff[p] : 0;
+    const float nanv = __int_as_float(0x7fc00000);
+    int hs_pair = 0, why_h = 0, why_f = 0;
+    T dgcp_pair = 0;  // d log10 L / d gcp, summed over the tiles
     // the adjoint enters the pair's lanes one per step from its last column on: renormalise
     // after every one of the first ramp_b such steps (a window set by the pair alone, so the
     // result does not depend on which pairs share the warp), then at segment boundaries
     const int ramp_b = 16 + ((L + 15) & ~15);
-    // lane 0's row above its strip (row 0 of the DP, or a pad row): S = K0 D(0, j)
-    const T bndS = t == 0 ? bnd : (T)0;
+    for (int tile = ntile - 1; tile >= 0; --tile) {
+      const bool last_tile = tile == ntile - 1;
+      // the tile below's partials and first-row adjoints (and phase A's rows) are in memory
+      __syncwarp();
+      setup_tile(tile);
+      T *ckt = ckb + (size_t)tile * a.ck_tile;
+      // pad rows: the rows above row 1 (their partials are never used)
+      const int first = npad - tile * LK - t * K;  // local index of the lane's first real row
+      // lanes whose products can matter: those holding a real row, and the pad lane just
+      // above a first real row that starts a lane (its last row's S feeds that row's beta
+      // partial)
+      const bool real_lane = first <= K;
+      // Coefficients of the row just below the strip (the lower lane's row 0, unbiased); the
+      // last lane of a tile above another takes the next tile's first row
+      T apb = __shfl_down_sync(FULL, ap[0], 1, L);
+      T dlb = __shfl_down_sync(FULL, dl[0], 1, L);
+      T eib = __shfl_down_sync(FULL, ei[0], 1, L);
+      const TileCol<T> *above = nullptr, *ain = nullptr;
+      TileCol<T> *aout = nullptr;
+      if constexpr (TILED) {
+        if (tile > 0) {
+          above = fbuf + (size_t)(tile - 1) * a.tile_cols;
+          aout = abuf + (size_t)(tile & 1) * a.tile_cols;
+        }
+        if (!last_tile) {
+          ain = abuf + (size_t)((tile + 1) & 1) * a.tile_cols;
+          if (t == L - 1) {
+            const int64_t gb = r0 + (int64_t)(tile + 1) * LK - npad;
+            T zdum, Qdum, epb = eps, beb = beta;
+            if constexpr (GQ) row_gap<T>(fa, gb, epb, beb);
+            row_params<T>(fa, gb, apb, dlb, zdum, Qdum, GQ ? (double)beb : 0.0);
+            eib = epb;
+          }
+        }
+      }
+      AdjState<T, K> as;
+#pragma unroll
+      for (int r = 0; r < K; ++r) as.u[r] = as.Db[r] = 0;
+      as.Itop = as.diagU = 0;
+      as.EB = (last_tile && t == L - 1) ? -ES : 0;
+      as.fB = 0;
+      as.seed = 0;
+      as.nz = false;
+      // the seed 1/L enters at row m only (the last tile's last lane)
+      const T Sseed = (last_tile && okS) ? S : (T)0;
+      adj_rescale<T, L, K, kBias>(as, t, Sseed, ES);
+      // Partial sums, each held as (true value) x 2^-H, the lane's accumulator scale.
+      // Per row r: gA (alpha_r: u(r,j+1) M(r-1,j)), gD (delta_r: I^(r,j) M(r-1,j)),
+      // gZ (zeta_r: D^(r,j+1) M(r,j)), gY (M^(r,j) M(r,j)), gX (its mismatch-column part
+      // times -e_mismatch).  gAl / gDl: the products for the lower lane's row 0.
+      // Lane scalars: gS (beta: u S of the row above), gEI (eps via I), gED (eps via D).
+      // With a per-base track the lane scalars are kept per row instead: gSr (beta_r),
+      // gEIr and gEDr (eps_r), with gSl / gEIl the lower lane's row 0.
+      T gA[K], gD[K], gZ[K], gY[K], gX[K];
+#pragma unroll
+      for (int r = 0; r < K; ++r) gA[r] = gD[r] = gZ[r] = gY[r] = gX[r] = 0;
+      T gAl = 0, gDl = 0, gS = 0, gEI = 0, gED = 0;
+      T gSr[GQ ? K : 1], gEIr[GQ ? K : 1], gEDr[GQ ? K : 1], gSl = 0, gEIl = 0;
+#pragma unroll
+      for (int r = 0; r < (GQ ? K : 1); ++r) gSr[r] = gEIr[r] = gEDr[r] = 0;
+      int H = kNoScale;
+      // lane 0's row above its strip (row 0 of the DP, or a pad row): S = K0 D(0, j); below
+      // the first tile that row is the tile above's last row, whose lane forms the product
+      const T bndS = (t == 0 && tile == 0) ? bnd : (T)0;
+      // the last lane of a tile above another: the tile below's first-row adjoints of the
+      // segment's columns (lane u: the column of reverse step b + u), and the exponent and
+      // size of the next ones to arrive (for the lane's renormalisation)
+      TileCol<T> ab = {0, 0, 0, 0};
+      int Eo = 0;
+      T xo = 0;
+      // until the first nonzero adjoint arrives from the tile below, that lane's state is all
+      // zero: it then takes the exponent that brings the arriving values near 1
+      bool got_in = false;
 
-    // the lanes' codes of each segment's steps, loaded one segment ahead as in phase A
-    segc = seg_codes(nq - 1);
-    bool nz_next = nzA;  // the state after the last segment
-    // A segment's closing renormalisation is applied at the start of the next segment's
-    // reverse, when that segment's forward exponent EF is known: a lane then keeps
-    // EF + EB = H where it can, so its partial sums need no re-basing.
-    bool pend = false;
-    for (int q = nq - 1; q >= 0; --q) {
-      const int b = q < ramp ? q : ramp + kSeg * (q - ramp);
-      const int len = q < ramp ? 1 : kSeg;
-      const uint64_t codes = segc;
-      segc = seg_codes(q - 1);
-      bool nzq;
-      {
-        T ck[CKW];
-        rec_load<T, CKW, true>(ckb + (size_t)q * 32 * CKW, lane, ck);
-#pragma unroll
-        for (int r = 0; r < K; ++r) {
-          st.M[r] = ck[r];
-          st.I[r] = ck[K + r];
-          st.D[r] = ck[2 * K + r];
-        }
-        st.Md = ck[3 * K];
-        st.Sd = ck[3 * K + 1];
-        st.f = ck[3 * K + 2];
-        const int ef = bits_int<T>(ck[3 * K + 3]);
-        st.E = ef >> 1;
-        nzq = (ef & 1) != 0;
-      }
-      // bring the next (left) segment's checkpoint from DRAM towards L2 while this one runs
-      if (q > 0 && lane == 0) prefetch_l2(ckb + (size_t)(q - 1) * 32 * CKW, 32 * CKW * sizeof(T));
-      // forward values in the lane over this segment: nonzero at its start or at its end (a
-      // lane's state turns nonzero once and stays so; power-of-two rescaling keeps zeros)
-      const bool nzF = nzq || nz_next;
-      nz_next = nzq;
-      // recompute the segment, recording the lane's rows after each step (column b+u2+1-t)
-      for (int u2 = 0; u2 < len; ++u2) {
-        const int cu = code_at(codes, u2);
-        T in3[3];
-        wf_step<T, L, K, true, true, true, false, true>(st, cu, t, bnd, eps, tblE, ap, dl, zt,
-                                                        ei, in3);
-        if (u2 < len - 1) {  // the last step's state stays in registers
-          T rec[RW];
+      // the lanes' codes of each segment's steps, loaded one segment ahead as in phase A
+      uint64_t segc = seg_codes(nq - 1);
+      bool nz_next = (nz_end >> tile) & 1;  // the state after the last segment
+      // A segment's closing renormalisation is applied at the start of the next segment's
+      // reverse, when that segment's forward exponent EF is known: a lane then keeps
+      // EF + EB = H where it can, so its partial sums need no re-basing.
+      bool pend = false;
+      for (int q = nq - 1; q >= 0; --q) {
+        const int b = q < ramp ? q : ramp + kSeg * (q - ramp);
+        const int len = q < ramp ? 1 : kSeg;
+        const uint64_t codes = segc;
+        segc = seg_codes(q - 1);
+        bool nzq;
+        {
+          T ck[CKW];
+          rec_load<T, CKW, true>(ckt + (size_t)q * 32 * CKW, lane, ck);
 #pragma unroll
           for (int r = 0; r < K; ++r) {
-            rec[r] = st.M[r];
-            rec[K + r] = st.D[r];
+            st.M[r] = ck[r];
+            st.I[r] = ck[K + r];
+            st.D[r] = ck[2 * K + r];
           }
-          rec[2 * K] = st.I[0];
-#pragma unroll
-          for (int k = 2 * K + 1; k < RW; ++k) rec[k] = 0;
-          rec_store<T, RW>(recS + (size_t)u2 * 32 * RW, lane, rec);
+          st.Md = ck[3 * K];
+          st.Sd = ck[3 * K + 1];
+          st.f = ck[3 * K + 2];
+          const int ef = bits_int<T>(ck[3 * K + 3]);
+          st.E = ef >> 1;
+          nzq = (ef & 1) != 0;
         }
-      }
-      const int EF = st.E;
-      const T fS = bndS * Num<T>::exp2i(-EF);  // lane 0's boundary row in its own scale
-      if (__any_sync(FULL, pend))
-        adj_rescale<T, L, K, kBias>(as, t, okS ? S : (T)0, ES, pend, H != kNoScale, H - EF);
-      pend = false;
-      // reverse over the segment
-      for (int u2 = len - 1; u2 >= 0; --u2) {
-        const int64_t j = (int64_t)b + u2 + 1 - t;  // this lane's column at this step
-        const int c = code_at(codes, u2);
-        // forward values of the lane's rows at column j: M, I, D/zeta (rec[r], [K+r], [2K+r])
-        T rec[3 * K];
-        if (u2 == len - 1) {
-#pragma unroll
-          for (int r = 0; r < K; ++r) {
-            rec[r] = st.M[r];
-            rec[K + r] = st.I[r];
-            rec[2 * K + r] = st.D[r];
+        // bring the next (left) segment's checkpoint from DRAM towards L2 while this one runs
+        if (q > 0 && lane == 0)
+          prefetch_l2(ckt + (size_t)(q - 1) * 32 * CKW, 32 * CKW * sizeof(T));
+        // forward values in the lane over this segment: nonzero at its start or at its end (a
+        // lane's state turns nonzero once and stays so; power-of-two rescaling keeps zeros)
+        const bool nzF = nzq || nz_next;
+        nz_next = nzq;
+        TileCol<T> cb = {0, 0, 0, 0};
+        if constexpr (TILED) {
+          cb = load_above(above, b);
+          if (ain) {
+            // reverse step b + u of the last lane is at column b + u + 2 - L
+            const int64_t c = (int64_t)b + lane + 1 - L;
+            ab = (lane < kSeg && c >= 0 && c < n) ? ain[c] : TileCol<T>{0, 0, 0, 0};
+            const T nM = __shfl_sync(FULL, ab.M, len - 1), nI = __shfl_sync(FULL, ab.I, len - 1);
+            Eo = (int)__shfl_sync(FULL, ab.E, len - 1);
+            xo = fmax(fabs(nM), nI);
           }
-        } else {
-          T sr[RW];
-          rec_load<T, RW>(recS + (size_t)u2 * 32 * RW, lane, sr);
-#pragma unroll
-          for (int r = 0; r < K; ++r) {
-            rec[r] = sr[r];
-            rec[2 * K + r] = sr[K + r];
-          }
-          rec[K] = sr[2 * K];
-#pragma unroll
-          for (int r = 1; r < K; ++r) rec[K + r] = dl[r] * rec[r - 1] + ei[r] * rec[K + r - 1];
         }
-        T e[K];
-        load_rows<T, K>(tblE + c * CS, e);
-        T rU = __shfl_down_sync(FULL, as.u[0], 1, L);
-        T rI = __shfl_down_sync(FULL, as.Itop, 1, L);
-        if (t == L - 1) {
-          rU = 0;
-          rI = 0;
-        } else {
-          rU *= as.fB;
-          rI *= as.fB;
-        }
-        const T ubK = as.diagU;
-        as.diagU = rU;
-        const T sd = (t == L - 1 && j >= 1 && j <= n) ? as.seed : (T)0;
-        // Posterior scale 2^(EF + EB): products of stored forward and adjoint values are
-        // accumulated raw, the accumulators re-based when the scale changes.  Lanes whose
-        // forward or adjoint values are all zero contribute nothing; h > kHmax with both
-        // nonzero means forward and adjoint mass sit in disjoint cells of the lane, beyond
-        // the type's range: the pair goes to FP64.
-        const int h = EF + as.EB;
-        const bool nzB = as.nz || rU != (T)0 || rI != (T)0 || sd != (T)0;
-        const bool live = real_lane && nzF && nzB;
-        if (live && h > kHmax) hard = true;
-        // A step whose posterior scale is negligible (h < kHmin) adds its products at scale
-        // kHmin: each is then counted 2^(kHmin - h) times too large, yet stays below
-        // 2^(16 + kHmin) of a posterior, far under the rounding of the sums it joins.  Every
-        // lane runs the same code, with no per-step zeroing.
-        const int hq = h < kHmin ? kHmin : h;
-        if (live && hq <= kHmax && hq != H) {
-          // re-base the sums from 2^-H to 2^-hq (all zero while H is unset); a shift beyond
-          // the type's exponent range is applied in two exact halves
-          auto rebase = [&](T sc) {
+        // recompute the segment, recording the lane's rows after each step (column b+u2+1-t)
+        for (int u2 = 0; u2 < len; ++u2) {
+          fstep(code_at(codes, u2), u2, cb, above != nullptr);
+          if (u2 < len - 1) {  // the last step's state stays in registers
+            T rec[RW];
 #pragma unroll
             for (int r = 0; r < K; ++r) {
-              gA[r] *= sc;
-              gD[r] *= sc;
-              gZ[r] *= sc;
-              gY[r] *= sc;
-              gX[r] *= sc;
+              rec[r] = st.M[r];
+              rec[K + r] = st.D[r];
             }
-            gAl *= sc;
-            gDl *= sc;
-            gS *= sc;
-            gEI *= sc;
-            gED *= sc;
-          };
-          if (H != kNoScale) {
-            int d = H - hq;
-            if (d > kHmax + 20 || d < -(kHmax + 20)) {
-              rebase(Num<T>::exp2i(d / 2));
-              d -= d / 2;
-            }
-            rebase(Num<T>::exp2i(d));
-          }
-          H = hq;
-        }
-        // Lanes that are not live add zeros (all forward or all adjoint values zero), garbage
-        // that is discarded (pad lanes) or garbage of a pair that goes to FP64 (h > kHmax):
-        // no per-row branch.
-        T ub = ubK, Ibl = rI;
-        {
+            rec[2 * K] = st.I[0];
 #pragma unroll
-          for (int r = K - 1; r >= 0; --r) {
-            const T apB = r == K - 1 ? apb : ap[r + 1];
-            const T dlB = r == K - 1 ? dlb : dl[r + 1];
-            const T eiB = r == K - 1 ? eib : ei[r + 1];
-            const T uba = fabs(ub);       // u(r+1, j+1); u carries the emission's sign
-            const T zD = zt[r] * as.Db[r];
-            const T Mv = rec[r], Iv = rec[K + r], Dv = rec[2 * K + r];  // forward, column j
-            // M^(r, j); the last row of the last lane adds the seed 1/L (no addition of a
-            // zero elsewhere: x + 0 is not free in IEEE arithmetic)
-            const T Mb0 = fma(apB, uba, fma(dlB, Ibl, zD));
-            const T Mb = r == K - 1 ? Mb0 + sd : Mb0;
-            // I^(r, j): one FMA on the row-to-row chain; eps x I^(r+1, j) again for the partial
-            const T Ib = fma(eiB, Ibl, r == K - 1 ? uba + sd : uba);
-            const T Il = eiB * Ibl;
-            const T Dn = uba + eps * as.Db[r];                           // D^(r, j)
-            const T un = e[r] * Mb;                                      // u(r, j)
-            {
-              if (r == K - 1) {
-                gAl += uba * Mv;
-                gDl += Ibl * Mv;
-              } else {
-                gA[r + 1] += uba * Mv;
-                gD[r + 1] += Ibl * Mv;
+            for (int k = 2 * K + 1; k < RW; ++k) rec[k] = 0;
+            rec_store<T, RW>(recS + (size_t)u2 * 32 * RW, lane, rec);
+          }
+        }
+        const int EF = st.E;
+        const T fS = bndS * Num<T>::exp2i(-EF);  // lane 0's boundary row in its own scale
+        if (__any_sync(FULL, pend))
+          adj_rescale<T, L, K, kBias>(as, t, Sseed, ES, pend, H != kNoScale, H - EF,
+                                      ain != nullptr, Eo, xo);
+        pend = false;
+        // reverse over the segment
+        for (int u2 = len - 1; u2 >= 0; --u2) {
+          const int64_t j = (int64_t)b + u2 + 1 - t;  // this lane's column at this step
+          const int c = code_at(codes, u2);
+          // forward values of the lane's rows at column j: M, I, D/zeta (rec[r], [K+r], [2K+r])
+          T rec[3 * K];
+          if (u2 == len - 1) {
+#pragma unroll
+            for (int r = 0; r < K; ++r) {
+              rec[r] = st.M[r];
+              rec[K + r] = st.I[r];
+              rec[2 * K + r] = st.D[r];
+            }
+          } else {
+            T sr[RW];
+            rec_load<T, RW>(recS + (size_t)u2 * 32 * RW, lane, sr);
+#pragma unroll
+            for (int r = 0; r < K; ++r) {
+              rec[r] = sr[r];
+              rec[2 * K + r] = sr[K + r];
+            }
+            rec[K] = sr[2 * K];
+#pragma unroll
+            for (int r = 1; r < K; ++r) rec[K + r] = dl[r] * rec[r - 1] + ei[r] * rec[K + r - 1];
+          }
+          T e[K];
+          load_rows<T, K>(tblE + c * CS, e);
+          T rU = __shfl_down_sync(FULL, as.u[0], 1, L);
+          T rI = __shfl_down_sync(FULL, as.Itop, 1, L);
+          bool adopt_now = false;  // the exponent changed: every lane's factors are renewed
+          if (TILED && ain) {  // warp-uniform (one pair per warp)
+            // the tile below's lane 0 at this column, converted to this lane's scale
+            const T bM = __shfl_sync(FULL, ab.M, u2), bI = __shfl_sync(FULL, ab.I, u2);
+            const int bE = (int)__shfl_sync(FULL, ab.E, u2);
+            if (t == L - 1) {
+              xo = fmax(fabs(bM), bI);
+              Eo = bE;
+              if (!got_in && xo > (T)0) {
+                as.EB = bE - kBias * (K - 1) + Num<T>::ilog2(xo);
+                got_in = true;
+                adopt_now = true;
               }
-              gS += uba * (Iv + zt[r] * Dv);
-              // the I -> I partial counts only where the row below is a real row (pad rows
-              // pass the boundary down with a nonzero coefficient)
-              gEI += (r + 1 > first ? Il : (T)0) * Iv;
-              gZ[r] += as.Db[r] * Mv;
-              gED += zD * Dv;
-              gY[r] += Mb * Mv;
-              gX[r] += fmin(un, (T)0) * Mv;
+              const T cvB = Num<T>::exp2i(bE - as.EB - kBias * (K - 1));
+              rU = bM * cvB;
+              rI = bI * cvB;
+            } else {
+              rU *= as.fB;
+              rI *= as.fB;
             }
-            ub = as.u[r];
-            as.u[r] = un;
-            as.Db[r] = Dn;
-            Ibl = Ib;
+          } else {
+            if (t == L - 1) {
+              rU = 0;
+              rI = 0;
+            } else {
+              rU *= as.fB;
+              rI *= as.fB;
+            }
           }
-          // lane 0's row above: u(0, j+1) times the boundary S = K0 D(0, j)
-          gS += fabs(ub) * fS;
+          const T ubK = as.diagU;
+          as.diagU = rU;
+          const T sd = (t == L - 1 && j >= 1 && j <= n) ? as.seed : (T)0;
+          // Posterior scale 2^(EF + EB): products of stored forward and adjoint values are
+          // accumulated raw, the accumulators re-based when the scale changes.  Lanes whose
+          // forward or adjoint values are all zero contribute nothing; h > kHmax with both
+          // nonzero means forward and adjoint mass sit in disjoint cells of the lane, beyond
+          // the type's range: the pair goes to FP64.
+          const int h = EF + as.EB;
+          const bool nzB = as.nz || rU != (T)0 || rI != (T)0 || sd != (T)0;
+          const bool live = real_lane && nzF && nzB;
+          if (live && h > kHmax) hard = true;
+          // A step whose posterior scale is negligible (h < kHmin) adds its products at scale
+          // kHmin: each is then counted 2^(kHmin - h) times too large, yet stays below
+          // 2^(16 + kHmin) of a posterior, far under the rounding of the sums it joins.
+          // Every lane runs the same code, with no per-step zeroing.
+          const int hq = h < kHmin ? kHmin : h;
+          if (live && hq <= kHmax && hq != H) {
+            // re-base the sums from 2^-H to 2^-hq (all zero while H is unset); a shift beyond
+            // the type's exponent range is applied in two exact halves
+            auto rebase = [&](T sc) {
+#pragma unroll
+              for (int r = 0; r < K; ++r) {
+                gA[r] *= sc;
+                gD[r] *= sc;
+                gZ[r] *= sc;
+                gY[r] *= sc;
+                gX[r] *= sc;
+              }
+              gAl *= sc;
+              gDl *= sc;
+              gS *= sc;
+              gEI *= sc;
+              gED *= sc;
+              if constexpr (GQ) {
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                  gSr[r] *= sc;
+                  gEIr[r] *= sc;
+                  gEDr[r] *= sc;
+                }
+                gSl *= sc;
+                gEIl *= sc;
+              }
+            };
+            if (H != kNoScale) {
+              int d = H - hq;
+              if (d > kHmax + 20 || d < -(kHmax + 20)) {
+                rebase(Num<T>::exp2i(d / 2));
+                d -= d / 2;
+              }
+              rebase(Num<T>::exp2i(d));
+            }
+            H = hq;
+          }
+          // Lanes that are not live add zeros (all forward or all adjoint values zero),
+          // garbage that is discarded (pad lanes) or garbage of a pair that goes to FP64
+          // (h > kHmax): no per-row branch.
+          T ub = ubK, Ibl = rI;
+          {
+#pragma unroll
+            for (int r = K - 1; r >= 0; --r) {
+              const T apB = r == K - 1 ? apb : ap[r + 1];
+              const T dlB = r == K - 1 ? dlb : dl[r + 1];
+              const T eiB = r == K - 1 ? eib : ei[r + 1];
+              const T uba = fabs(ub);       // u(r+1, j+1); u carries the emission's sign
+              const T zD = zt[r] * as.Db[r];
+              const T Mv = rec[r], Iv = rec[K + r], Dv = rec[2 * K + r];  // forward, column j
+              // M^(r, j); the last row of the last lane adds the seed 1/L (no addition of a
+              // zero elsewhere: x + 0 is not free in IEEE arithmetic)
+              const T Mb0 = fma(apB, uba, fma(dlB, Ibl, zD));
+              const T Mb = r == K - 1 ? Mb0 + sd : Mb0;
+              // I^(r, j): one FMA on the row-to-row chain; eps x I^(r+1, j) again for the
+              // partial
+              const T Ib = fma(eiB, Ibl, r == K - 1 ? uba + sd : uba);
+              const T Il = eiB * Ibl;
+              const T Dn = uba + (GQ ? er[r] : eps) * as.Db[r];            // D^(r, j)
+              const T un = e[r] * Mb;                                      // u(r, j)
+              {
+                if (r == K - 1) {
+                  gAl += uba * Mv;
+                  gDl += Ibl * Mv;
+                } else {
+                  gA[r + 1] += uba * Mv;
+                  gD[r + 1] += Ibl * Mv;
+                }
+                // the I -> I partial counts only where the row below is a real row (pad rows
+                // pass the boundary down with a nonzero coefficient)
+                if constexpr (GQ) {
+                  if (r == K - 1) {
+                    gSl += uba * (Iv + zt[r] * Dv);
+                    gEIl += (r + 1 > first ? Il : (T)0) * Iv;
+                  } else {
+                    gSr[r + 1] += uba * (Iv + zt[r] * Dv);
+                    gEIr[r + 1] += (r + 1 > first ? Il : (T)0) * Iv;
+                  }
+                  gEDr[r] += zD * Dv;
+                } else {
+                  gS += uba * (Iv + zt[r] * Dv);
+                  gEI += (r + 1 > first ? Il : (T)0) * Iv;
+                  gED += zD * Dv;
+                }
+                gZ[r] += as.Db[r] * Mv;
+                gY[r] += Mb * Mv;
+                gX[r] += fmin(un, (T)0) * Mv;
+              }
+              ub = as.u[r];
+              as.u[r] = un;
+              as.Db[r] = Dn;
+              Ibl = Ib;
+            }
+            // lane 0's row above: u(0, j+1) times the boundary S = K0 D(0, j)
+            if constexpr (GQ) gSr[0] += fabs(ub) * fS;
+            else gS += fabs(ub) * fS;
+          }
+          as.Itop = Ibl;
+          if constexpr (TILED) {
+            // this tile's first row adjoints for the tile above (before any renormalisation)
+            if (aout && t == 0 && j >= 1 && j <= n) {
+              TileCol<T> o;
+              o.M = as.u[0];
+              o.I = as.Itop;
+              o.X = 0;
+              o.E = (T)as.EB;
+              aout[j - 1] = o;
+            }
+          }
+          const int sf = b + u2 + 1;  // forward step just reversed
+          // Inside the adjoint's ramp (the first ramp_b steps from the pair's last column, a
+          // window set by the pair alone) a lane without adjoint mass renormalises after every
+          // step, to adopt the exponent of the values about to arrive; every lane
+          // renormalises at the segment's end (deferred to the next segment's start).
+          const bool apply = (sf <= fin && sf > fin - ramp_b && !as.nz) || adopt_now;
+          if (u2 == 0) pend = sf <= fin && !apply;
+          if (__any_sync(FULL, apply))
+            adj_rescale<T, L, K, kBias>(as, t, Sseed, ES, apply, false, 0, ain != nullptr, Eo,
+                                        xo);
         }
-        as.Itop = Ibl;
-        const int sf = b + u2 + 1;  // forward step just reversed
-        // Inside the adjoint's ramp (the first ramp_b steps from the pair's last column, a
-        // window set by the pair alone) a lane without adjoint mass renormalises after every
-        // step, to adopt the exponent of the values about to arrive; every lane renormalises
-        // at the segment's end (deferred to the next segment's start).
-        const bool apply = sf <= fin && sf > fin - ramp_b && !as.nz;
-        if (u2 == 0) pend = sf <= fin && !apply;
-        if (__any_sync(FULL, apply)) adj_rescale<T, L, K, kBias>(as, t, okS ? S : (T)0, ES, apply);
       }
-    }
 
-    // ---- phase C: chain rule to the Phred inputs, per-pair partials ------------------------
-    // accumulators to true values; the products of a row's I^ with the row above's M carry
-    // one row bias less than the others (x 2^kBias), except across the lane edge
-    const T sc = H == kNoScale ? (T)0 : Num<T>::exp2i(H);
-    gAl *= sc;
-    gDl *= sc;
-    T dAlpha[K], dDelta[K];
+      // ---- phase C: chain rule to the Phred inputs, per-pair partials of the tile's rows --
+      // accumulators to true values; the products of a row's I^ with the row above's M
+      // carry one row bias less than the others (x 2^kBias), except across the lane edge
+      const T sc = H == kNoScale ? (T)0 : Num<T>::exp2i(H);
+      gAl *= sc;
+      gDl *= sc;
+      T dAlpha[K], dDelta[K];
 #pragma unroll
-    for (int r = 0; r < K; ++r) {
-      dAlpha[r] = gA[r] * sc;
-      dDelta[r] = gD[r] * (sc * (T)(1 << kBias));
-      gZ[r] *= sc;
-      gY[r] *= sc;
-      gX[r] *= sc;
-    }
-    {
-      const T aup = __shfl_up_sync(FULL, gAl, 1, L);
-      const T dup = __shfl_up_sync(FULL, gDl, 1, L);
-      dAlpha[0] = t == 0 ? (T)0 : aup;
-      dDelta[0] = t == 0 ? (T)0 : dup;
-    }
-    // pad lanes' scalar sums are garbage by construction
-    T gSs = real_lane ? gS * sc : (T)0, gEs = real_lane ? (gED + gEI / eps) * sc : (T)0;
-    if (t == 0 && first <= K) {
-      // Lane 0 never visits column 0, so when lane 0 holds row 1 or the row above it, the
-      // beta term of M(1,1) = lambda beta D(0,0), u(1,1) S(0,0), is added here: the reverse
-      // sweep ended at column 1 (as.u holds u(., 1); as.diagU the lower lane's u(row 0, 1)),
-      // and S(0,0) is the row above row 1 at column 0 in the initial scale (E = 0): the
-      // boundary K0/n, times the pad pass-through bias when row 1 is not the lane's row 0.
-      T uf = first == K ? fabs(as.diagU) : (T)0;
+      for (int r = 0; r < K; ++r) {
+        dAlpha[r] = gA[r] * sc;
+        dDelta[r] = gD[r] * (sc * (T)(1 << kBias));
+        gZ[r] *= sc;
+        gY[r] *= sc;
+        gX[r] *= sc;
+      }
+      {
+        const T aup = __shfl_up_sync(FULL, gAl, 1, L);
+        const T dup = __shfl_up_sync(FULL, gDl, 1, L);
+        dAlpha[0] = t == 0 ? (T)0 : aup;
+        dDelta[0] = t == 0 ? (T)0 : dup;
+      }
+      // pad lanes' scalar sums are garbage by construction
+      T gSs = real_lane ? gS * sc : (T)0, gEs = real_lane ? (gED + gEI / eps) * sc : (T)0;
+      T spec = 0;  // the beta term of M(1,1), true value (see below)
+      if (t == 0 && tile == 0 && first <= K) {
+        // Lane 0 never visits column 0, so when lane 0 holds row 1 or the row above it, the
+        // beta term of M(1,1) = lambda beta D(0,0), u(1,1) S(0,0), is added here: the reverse
+        // sweep ended at column 1 (as.u holds u(., 1); as.diagU the lower lane's u(row 0, 1)),
+        // and S(0,0) is the row above row 1 at column 0 in the initial scale (E = 0): the
+        // boundary K0/n, times the pad pass-through bias when row 1 is not the lane's row 0.
+        T uf = first == K ? fabs(as.diagU) : (T)0;
 #pragma unroll
-      for (int r = 0; r < K; ++r)
-        if (r == first) uf = fabs(as.u[r]);
-      const T S00 = first == 0 ? bnd : bnd * (T)(1ll << (kBias * (first - 1)));
-      gSs += (uf * S00) * Num<T>::exp2i(as.EB / 2) * Num<T>::exp2i(as.EB - as.EB / 2);
-    }
-    bool finite = true;  // over the real rows (pad rows' sums are never used)
-#pragma unroll
-    for (int r = 0; r < K; ++r)
-      if (r >= first)
-        finite = finite && fabs(dAlpha[r]) < (T)1e30 && fabs(dDelta[r]) < (T)1e30 &&
-                 fabs(gZ[r]) < (T)1e30 && fabs(gY[r]) < (T)1e30 &&
-                 fabs(gX[r]) < (T)1e30;  // false for NaN too
-    int hs_any = (hard || !finite) ? 1 : 0;
-    int why_h = hard ? 1 : 0, why_f = finite ? 0 : 1;
-#pragma unroll
-    for (int o = 1; o < L; o <<= 1) {
-      gSs += __shfl_xor_sync(FULL, gSs, o, L);
-      gEs += __shfl_xor_sync(FULL, gEs, o, L);
-      hs_any |= __shfl_xor_sync(FULL, hs_any, o, L);
-      why_h |= __shfl_xor_sync(FULL, why_h, o, L);
-      why_f |= __shfl_xor_sync(FULL, why_f, o, L);
-    }
-    // d ln L / d eps = gE - gS / beta (beta = 1 - eps); d eps / d gcp = -(ln 10 / 10) eps
-    const T dgcp_l = -(gEs - gSs / beta) * eps * (T)0.1;
-    if (!(fabs(dgcp_l) < (T)1e30)) hs_any = 1;
-    if (valid && bad && a.out && t == 0) {
-      a.out[p] = __longlong_as_double(0x7ff8000000000000ll);
-      a.oflags[p] = PHMM_FLAG_INVALID;
-    }
-    if (valid && !bad) {
-      const bool to_rescue = hs_any && !a.rescue;
-      if (to_rescue) {
-        if (t == 0) {
-          const int bin = bin64_of_m(m);
-          const int pos = atomicAdd(&a.resc_count[bin], 1);
-          a.resc_list[bin][pos] = p;
-          if (a.why) {
-            if (why_h) atomicAdd(&a.why[0], 1);
-            if (why_f) atomicAdd(&a.why[1], 1);
-          }
-        }
-      } else {
-        const double dy = a.dL ? a.dL[p] : 1.0;
-        const int64_t po = a.poff[p];
-        if (a.out && t == 0) {
-          // log10 L = log10(S) + (ES - kBias (K-1)) log10 2, as the forward's per-lane-exponent
-          // tier writes it
-          constexpr double LOG10_2 = 0.301029995663981195213738894724493027;
-          a.out[p] = log10((double)S) + (double)(ES - kBias * (K - 1)) * LOG10_2;
-          a.oflags[p] = (uint8_t)(sizeof(T) == 4 ? PHMM_FLAG_FP32 : PHMM_FLAG_RESCUED64) |
-                        (uint8_t)PHMM_FLAG_EXTENDED;
-        }
-        const bool ok = !hs_any;
-        const float nanv = __int_as_float(0x7fc00000);
+        for (int r = 0; r < K; ++r)
+          if (r == first) uf = fabs(as.u[r]);
+        const T S00 = first == 0 ? bnd : bnd * (T)(1ll << (kBias * (first - 1)));
+        spec = (uf * S00) * Num<T>::exp2i(as.EB / 2) * Num<T>::exp2i(as.EB - as.EB / 2);
+        gSs += spec;
+      }
+      // With a per-base track: d log10 L / d gcp_r of the lane's rows, from the per-row sums
+      // (the lower lane's row 0 receives this lane's gSl / gEIl; row 1 the M(1,1) term) and,
+      // for the last lane of a tile above another, the same for the next tile's first row.
+      T dgq[GQ ? K : 1];
+      T dgq_next = 0;
+      if constexpr (GQ) {
+        const T upS = __shfl_up_sync(FULL, gSl * sc, 1, L);
+        const T upE = __shfl_up_sync(FULL, gEIl * sc, 1, L);
+        const T specUp = __shfl_up_sync(FULL, spec, 1, L);
+        const int firstUp = __shfl_up_sync(FULL, first, 1, L);
+        gSs = 0;
+        gEs = 0;
 #pragma unroll
         for (int r = 0; r < K; ++r) {
-          const int pos = t * K + r - npad;
+          const int pos = tile * LK + t * K + r - npad;
+          T Sr = gSr[r] * sc, Er = gEDr[r] * sc + gEIr[r] * sc / er[r];
+          if (r == 0 && t > 0) {
+            Sr += upS;
+            Er += upE / er[0];
+            if (t == 1 && tile == 0 && firstUp == K) Sr += specUp;
+          }
+          if (t == 0 && r == first) Sr += spec;
+          dgq[r] = 0;
+          if (pos >= 0) {
+            T epr, ber;
+            row_gap<T>(fa, r0 + pos, epr, ber);
+            dgq[r] = -(Er - Sr / ber) * epr * (T)0.1;
+            gSs += dgq[r];  // the lane's sum of d log10 L / d gcp_r
+          }
+        }
+        if (TILED && !last_tile && t == L - 1) {
+          const int64_t pos = (int64_t)(tile + 1) * LK - npad;
+          T epr, ber;
+          row_gap<T>(fa, r0 + pos, epr, ber);
+          dgq_next = -(gEIl * sc / epr - gSl * sc / ber) * epr * (T)0.1;
+          gSs += dgq_next;
+        }
+      }
+      bool finite = true;  // over the real rows (pad rows' sums are never used)
+#pragma unroll
+      for (int r = 0; r < K; ++r)
+        if (r >= first)
+          finite = finite && fabs(dAlpha[r]) < (T)1e30 && fabs(dDelta[r]) < (T)1e30 &&
+                   fabs(gZ[r]) < (T)1e30 && fabs(gY[r]) < (T)1e30 &&
+                   fabs(gX[r]) < (T)1e30;  // false for NaN too
+      if (TILED && !last_tile && t == L - 1)
+        finite = finite && fabs(gAl) < (T)1e30 && fabs(gDl) < (T)1e30 &&
+                 fabs(dgq_next) < (T)1e30;
+      if constexpr (GQ) {
+#pragma unroll
+        for (int r = 0; r < K; ++r)
+          if (r >= first) finite = finite && fabs(dgq[r]) < (T)1e30;
+      }
+      int hs_any = (hard || !finite) ? 1 : 0;
+      int wh = hard ? 1 : 0, wf = finite ? 0 : 1;
+#pragma unroll
+      for (int o = 1; o < L; o <<= 1) {
+        gSs += __shfl_xor_sync(FULL, gSs, o, L);
+        gEs += __shfl_xor_sync(FULL, gEs, o, L);
+        hs_any |= __shfl_xor_sync(FULL, hs_any, o, L);
+        wh |= __shfl_xor_sync(FULL, wh, o, L);
+        wf |= __shfl_xor_sync(FULL, wf, o, L);
+      }
+      // d ln L / d eps = gE - gS / beta (beta = 1 - eps); d eps / d gcp = -(ln 10 / 10) eps
+      // (with a per-base track gSs already holds the sum of the rows' d log10 L / d gcp_r)
+      const T dgcp_l = GQ ? gSs : -(gEs - gSs / beta) * eps * (T)0.1;
+      if (!(fabs(dgcp_l) < (T)1e30)) hs_any = 1;
+      hs_pair |= hs_any;
+      why_h |= wh;
+      why_f |= wf;
+      dgcp_pair += dgcp_l;
+      if (valid && !bad && !hs_pair) {
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+          const int pos = tile * LK + t * K + r - npad;
           if (pos < 0) continue;
-          T dum, del, zet, Q;
-          row_params<T>(fa, r0 + pos, dum, del, zet, Q);
-          const T gAlpha = dAlpha[r] / beta;  // d ln L / d alpha_r
+          T dum, del, zet, Q, epr = eps, ber = beta;
+          if constexpr (GQ) row_gap<T>(fa, r0 + pos, epr, ber);  // the row's beta
+          row_params<T>(fa, r0 + pos, dum, del, zet, Q, GQ ? (double)ber : 0.0);
+          const T gAlpha = dAlpha[r] / ber;  // d ln L / d alpha_r
           T di, dd;
           if (fa.alpha_mode) {
             const T iq = (T)qual_at(fa.iq, fa.qual_f32, r0 + pos);
@@ -739,16 +1018,83 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
           // lambda = 1 - Q on a match and Q / 3 on a mismatch.  gX holds -ex A2 with ex
           // the row's stored (biased) mismatch emission.
           const T bias = r ? (T)(1 << kBias) : (T)1;
-          const T ex = bias * (beta * (Q / (T)3));
+          const T ex = bias * (ber * (Q / (T)3));
           const T A2 = -gX[r] / ex;
           const T A1 = gY[r] - A2;
           // d log10 L / d bq = (d ln L / dQ) (-Q / 10)
           const T db = (A1 * (Q / ((T)1 - Q)) - A2) * (T)0.1;
-          a.part_bq[po + pos] = ok ? (float)(dy * (double)db) : nanv;
-          a.part_iq[po + pos] = ok ? (float)(dy * (double)di) : nanv;
-          a.part_dq[po + pos] = ok ? (float)(dy * (double)dd) : nanv;
+          a.part_bq[po + pos] = (float)(dy * (double)db);
+          a.part_iq[po + pos] = (float)(dy * (double)di);
+          a.part_dq[po + pos] = (float)(dy * (double)dd);
+          if constexpr (GQ) a.part_gq[po + pos] = (float)(dy * (double)dgq[r]);
         }
-        if (t == 0) a.pair_dgcp[p] = ok ? dy * (double)dgcp_l : (double)nanv;
+        if constexpr (TILED) {
+          // The tile below's first row: its alpha and delta partials pair its adjoints with
+          // this tile's last row (held by the last lane, which formed them); the tile below
+          // wrote the rest of that row's partials already.
+          if (!last_tile && t == L - 1) {
+            const int64_t pos = (int64_t)(tile + 1) * LK - npad;
+            T dum, del, zet, Q, epr = eps, ber = beta;
+            if constexpr (GQ) row_gap<T>(fa, r0 + pos, epr, ber);
+            row_params<T>(fa, r0 + pos, dum, del, zet, Q, GQ ? (double)ber : 0.0);
+            const T gAlpha = gAl / ber;
+            T di, dd;
+            if (fa.alpha_mode) {
+              const T iq = (T)qual_at(fa.iq, fa.qual_f32, r0 + pos);
+              const T dq = (T)qual_at(fa.dq, fa.qual_f32, r0 + pos);
+              const T pa = sizeof(T) == 4 ? (T)exp10f((float)(-(iq + dq) * (T)0.1))
+                                          : (T)exp10(-(double)(iq + dq) / 10.0);
+              di = -(gDl * del - gAlpha * pa) * (T)0.1;
+              dd = (gAlpha * pa) * (T)0.1;
+            } else {
+              di = -(gDl - gAlpha) * del * (T)0.1;
+              dd = gAlpha * zet * (T)0.1;
+            }
+            a.part_iq[po + pos] = (float)((double)a.part_iq[po + pos] + dy * (double)di);
+            a.part_dq[po + pos] = (float)((double)a.part_dq[po + pos] + dy * (double)dd);
+            if constexpr (GQ)
+              a.part_gq[po + pos] = (float)((double)a.part_gq[po + pos] + dy * (double)dgq_next);
+          }
+        }
+      }
+    }  // tiles
+
+    // ---- the pair's results -----------------------------------------------------------------
+    __syncwarp();  // partials written by other lanes of the warp, before any NaN fill
+    if (valid && bad && a.out && t == 0) {
+      a.out[p] = __longlong_as_double(0x7ff8000000000000ll);
+      a.oflags[p] = PHMM_FLAG_INVALID;
+    }
+    if (valid && !bad) {
+      const bool to_rescue = hs_pair && !a.rescue;
+      if (to_rescue) {
+        if (t == 0) {
+          const int bin = bin64_of_m(m);
+          const int pos = atomicAdd(&a.resc_count[bin], 1);
+          a.resc_list[bin][pos] = p;
+          if (a.why) {
+            if (why_h) atomicAdd(&a.why[0], 1);
+            if (why_f) atomicAdd(&a.why[1], 1);
+          }
+        }
+      } else {
+        if (a.out && t == 0) {
+          // log10 L = log10(S) + (ES - kBias (K-1)) log10 2, as the forward's per-lane-exponent
+          // tier writes it
+          constexpr double LOG10_2 = 0.301029995663981195213738894724493027;
+          a.out[p] = log10((double)S) + (double)(ES - kBias * (K - 1)) * LOG10_2;
+          a.oflags[p] = (uint8_t)(sizeof(T) == 4 ? PHMM_FLAG_FP32 : PHMM_FLAG_RESCUED64) |
+                        (uint8_t)PHMM_FLAG_EXTENDED;
+        }
+        if (hs_pair) {  // no finite gradient: every partial of the pair is NaN
+          for (int pos = t; pos < m; pos += L) {
+            a.part_bq[po + pos] = nanv;
+            a.part_iq[po + pos] = nanv;
+            a.part_dq[po + pos] = nanv;
+            if (GQ) a.part_gq[po + pos] = nanv;
+          }
+        }
+        if (t == 0) a.pair_dgcp[p] = hs_pair ? (double)nanv : dy * (double)dgcp_pair;
       }
     }
   }
@@ -763,6 +1109,9 @@ BwdKernel bwd32_lo(int L, int K);   // L in {4, 8}
 BwdKernel bwd32_mid(int L, int K);  // L = 16
 BwdKernel bwd32_hi(int L, int K);   // L = 32
 BwdKernel bwd64_table(int K);       // L = 32
+// per-base gap-continuation track: (16,4) (16,8) (32,8) (32,12) (32,16); FP64 32 x 4/8/16
+BwdKernel bwd32_gq(int L, int K);
+BwdKernel bwd64_gq(int K);
 
 #define PHMM_BWD_ROWS_SWITCH(T, L)             \
   switch (K) {                                 \

@@ -16,18 +16,20 @@ namespace phmm {
 int launch_validate(const phmm_batch &b, int64_t sum_m, int64_t sum_n, unsigned *err,
                     unsigned long long *cells, cudaStream_t s);
 int launch_prep(const phmm_batch &b, int64_t sum_m, float beta32, RowParams *rp,
-                uint8_t *rcode, uint8_t *hcode, cudaStream_t s, int *launches);
+                uint8_t *rcode, uint8_t *hcode, float2 *rgap, cudaStream_t s, int *launches);
 int launch_binning(const phmm_batch &b, const CfgTable &tab, int32_t *key, int32_t *counts,
                    int32_t *offsets, int32_t *cursor, int32_t *grp_begin, int32_t *grp_count,
                    int32_t *order, cudaStream_t s, int *launches);
 int bwd_enqueue_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, float *diq,
-                     float *ddq, double *dgcp, cudaStream_t s, int *launches,
+                     float *ddq, float *dgq, double *dgcp, cudaStream_t s, int *launches,
                      cudaEvent_t *ev3);
 int bwd_sweep_impl(phmm_plan *pl, char *ws, const double *dL, double *out, uint8_t *oflags,
                    cudaStream_t s, int *launches, cudaEvent_t *ev2);
 int bwd_reduce_impl(phmm_plan *pl, char *ws, const double *dL, float *dbq, float *diq,
-                    float *ddq, double *dgcp, cudaStream_t s, int *launches, cudaEvent_t ev1);
+                    float *ddq, float *dgq, double *dgcp, cudaStream_t s, int *launches,
+                    cudaEvent_t ev1);
 size_t bwd_workspace_bytes(const phmm_plan *pl);
+std::vector<size_t> bwd_guard_offsets(const phmm_plan *pl);
 int bwd_default_cfg(int m);
 int bwd_cfg_supported(int cfg);
 
@@ -101,10 +103,14 @@ static size_t table_warp_bytes(int K, int elem) {
   return (size_t)kCodes * 32 * LS * elem;
 }
 
-static FwdKernel get32(int cfg, bool ext) {
+static FwdKernel get32(int cfg, bool ext, bool gq = false) {
   const int L = cfg_lanes(cfg), K = cfg_rows(cfg);
+  if (gq) return ext ? fwd32_gq(L, K) : nullptr;
   if (L <= 8) return ext ? fwd32_ext_lo(L, K) : fwd32_plain_lo(L, K);
   return ext ? fwd32_ext_hi(L, K) : fwd32_plain_hi(L, K);
+}
+static FwdKernel get64(int cfg64, bool ext, bool gq = false) {
+  return gq ? fwd64_gq(rows64(cfg64), ext) : fwd64_table(rows64(cfg64), ext);
 }
 
 size_t fwd32_smem(int cfg, int block) { return (block / 32) * table_warp_bytes(cfg_rows(cfg), 4); }
@@ -114,45 +120,49 @@ size_t fwd64_smem(int cfg64, int block) {
 
 static std::once_flag g_attr_once;
 static void set_attrs() {
-  for (int cfg = 0; cfg < kNumCfg32; ++cfg)
-    for (int e = 0; e < 2; ++e) {
-      FwdKernel k = get32(cfg, e);
-      if (k) cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  227 * 1024);
-    }
-  for (int c = 0; c < kNumCfg64; ++c)
-    for (int e = 0; e < 2; ++e) {
-      FwdKernel k = fwd64_table(rows64(c), e);
-      if (k) cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  227 * 1024);
-    }
+  for (int g = 0; g < 2; ++g) {
+    for (int cfg = 0; cfg < kNumCfg32; ++cfg)
+      for (int e = 0; e < 2; ++e) {
+        FwdKernel k = get32(cfg, e, g);
+        if (k) cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    227 * 1024);
+      }
+    for (int c = 0; c < kNumCfg64; ++c)
+      for (int e = 0; e < 2; ++e) {
+        FwdKernel k = get64(c, e, g);
+        if (k) cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    227 * 1024);
+      }
+  }
 }
 
-int fwd32_blocks_per_sm(int cfg, bool ext, int block) {
+int fwd32_blocks_per_sm(int cfg, bool ext, int block, bool gq) {
   std::call_once(g_attr_once, set_attrs);
+  FwdKernel k = get32(cfg, ext, gq);
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, get32(cfg, ext), block,
-                                                fwd32_smem(cfg, block));
+  if (k) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, fwd32_smem(cfg, block));
   return nb;
 }
-int fwd64_blocks_per_sm(int cfg64, bool ext, int block) {
+int fwd64_blocks_per_sm(int cfg64, bool ext, int block, bool gq) {
   std::call_once(g_attr_once, set_attrs);
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd64_table(rows64(cfg64), ext), block,
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, get64(cfg64, ext, gq), block,
                                                 fwd64_smem(cfg64, block));
   return nb;
 }
 
+// The kernel of a launch follows its arguments: a batch with a per-base gap-continuation
+// track (a.gq) runs the kernels with per-row gap continuation.
 int launch_fwd32(int cfg, bool ext, int grid, int block, cudaStream_t s, const FwdArgs &a) {
   std::call_once(g_attr_once, set_attrs);
-  FwdKernel k = get32(cfg, ext);
+  FwdKernel k = get32(cfg, ext, a.gq != nullptr);
   if (!k) return (int)cudaErrorInvalidValue;
   k<<<grid, block, fwd32_smem(cfg, block), s>>>(a);
   return (int)cudaGetLastError();
 }
 int launch_fwd64(int cfg64, bool ext, int grid, int block, cudaStream_t s, const FwdArgs &a) {
   std::call_once(g_attr_once, set_attrs);
-  FwdKernel k = fwd64_table(rows64(cfg64), ext);
+  FwdKernel k = get64(cfg64, ext, a.gq != nullptr);
   if (!k) return (int)cudaErrorInvalidValue;
   k<<<grid, block, fwd64_smem(cfg64, block), s>>>(a);
   return (int)cudaGetLastError();
@@ -178,8 +188,20 @@ int default_cfg_of_m(int m) {
 
 using namespace phmm;
 
+// Debug builds (PHMM_DEBUG): a guard region of kGuardBytes after every workspace region, filled
+// with kGuardByte before each call and checked after it.
+constexpr size_t kGuardBytes = 256;
+constexpr unsigned char kGuardByte = 0xA5;
+#ifdef PHMM_DEBUG
+constexpr bool kDebug = true;
+#else
+constexpr bool kDebug = false;
+#endif
+
 struct WsLayout {
+  std::vector<size_t> guards;  // guard offsets (debug builds)
   size_t tile = 0;  // row-tile buffers (plans holding reads longer than one group)
+  size_t rgap = 0;  // per-position (eps_i, beta_i) (plans with a gap-continuation track)
   size_t rp, rcode, hcode, key, order, zero, zero_bytes, counts, ctr32, ctr64, ctrx, rcnt, xcnt,
       offsets, cursor, grp_begin, grp_count, rlist, xlist, bwd, total, why;
 };
@@ -189,6 +211,7 @@ struct phmm_plan {
   phmm_options o;
   int64_t sum_m = 0, sum_n = 0, cells = 0, pair_rows = 0, n_max = 0;
   int max_m = 0;
+  bool gq = false;  // the batch has a per-base gap-continuation track
   int cfg_of_m[PHMM_MAX_READ_LEN + 1];
   int bwd_cfg_of_m[PHMM_MAX_READ_LEN + 1];
   std::vector<int> used_cfgs, bwd_used;
@@ -199,6 +222,14 @@ struct phmm_plan {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t gexec = nullptr;
   void *g_ws = nullptr, *g_out = nullptr, *g_flags = nullptr;
+  // the fused training step's two calls, captured on small batches (pointer sets as keys)
+  cudaGraphExec_t gexec_fp = nullptr, gexec_bp = nullptr;
+  const void *gfp_key[3] = {nullptr, nullptr, nullptr};
+  const void *gbp_key[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // the previous call's pointers: a graph is captured only when a pointer set repeats
+  const void *gfp_prev[3] = {nullptr, nullptr, nullptr};
+  const void *gbp_prev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int gfp_launches = 0, gbp_launches = 0;
   // forward: FP32 kernels start/end, rescue end; adjoint: start, end, reduction end;
   // reduction start of the fused path
   cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -209,6 +240,7 @@ struct phmm_plan {
   bool timed = false;  // the latest forward recorded the timing events
   int launches_fwd = 0, launches_bwd = 0;
   void *bwd_state = nullptr;  // owned by the backward translation unit
+  unsigned *dbg_word = nullptr;  // debug builds: failed guard and index checks (device)
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -221,9 +253,14 @@ static void make_layout(phmm_plan *pl) {
   auto take = [&](size_t bytes) {
     size_t at = o;
     o = align256(o + bytes);
+    if (kDebug) {
+      L.guards.push_back(o);
+      o += kGuardBytes;
+    }
     return at;
   };
   L.rp = take(sizeof(RowParams) * std::max<int64_t>(pl->sum_m, 1));
+  if (pl->gq) L.rgap = take(sizeof(float2) * std::max<int64_t>(pl->sum_m, 1));
   L.rcode = take(std::max<int64_t>(pl->sum_m, 1));
   L.hcode = take((size_t)hap_code_bytes(pl->sum_n, pl->b.n_haps));
   L.key = take(4 * P);
@@ -246,6 +283,10 @@ static void make_layout(phmm_plan *pl) {
   o += 4 * 4;
   o = align256(o);
   L.zero_bytes = o - L.zero;
+  if (kDebug) {
+    L.guards.push_back(o);
+    o += kGuardBytes;
+  }
   L.offsets = take(4 * nkeys);
   L.cursor = take(4 * nkeys);
   L.grp_begin = take(4 * kNumCfg32);
@@ -258,8 +299,8 @@ static void make_layout(phmm_plan *pl) {
     const int block = 32 * pl->o.warps_per_block, c16 = cfg_index(32, 16);
     int bps = 1;
     for (int e = 0; e < 2; ++e) {
-      bps = std::max(bps, fwd32_blocks_per_sm(c16, e == 1, block));
-      bps = std::max(bps, fwd64_blocks_per_sm(2, e == 1, block));
+      bps = std::max(bps, fwd32_blocks_per_sm(c16, e == 1, block, pl->gq));
+      bps = std::max(bps, fwd64_blocks_per_sm(2, e == 1, block, pl->gq));
     }
     const size_t warps = (size_t)pl->sms * bps * (block / 32);
     L.tile = take(warps * 2 * (size_t)pl->n_max * 32);
@@ -298,6 +339,7 @@ const char *phmm_status_str(int s) {
     case PHMM_ENOMEM: return "workspace too small";
     case PHMM_ECUDA: return "CUDA error";
     case PHMM_ESTATE: return "call out of order";
+    case PHMM_EGUARD: return "debug build: a guard region or a kernel index check failed";
     default: return "unknown status";
   }
 }
@@ -329,6 +371,9 @@ int phmm_plan_create(const phmm_batch *batch, const phmm_options *opt, void *str
   if (b.alpha_mode != 0 && b.alpha_mode != 1) return PHMM_EINVAL;
   if (!(b.gcp > 0.0) || !std::isfinite(b.gcp)) return PHMM_EINVAL;
   if (o.first_line != PHMM_FIRST_PLAIN32 && o.first_line != PHMM_FIRST_EXT32) return PHMM_EINVAL;
+  // a per-base gap-continuation track runs the extended-range FP32 first line only
+  if (b.gcp_q && o.first_line != PHMM_FIRST_EXT32) return PHMM_EINVAL;
+  if (b.gcp_q && !o.binning) return PHMM_EINVAL;
   if (o.adjoint_rescue < 0 || o.adjoint_rescue > 2) return PHMM_EINVAL;
   if (!o.binning && !valid_group(o.lanes, o.rows)) return PHMM_EINVAL;
   (void)cudaGetLastError();  // drop a stale error left by an unrelated call
@@ -380,6 +425,7 @@ int phmm_plan_create(const phmm_batch *batch, const phmm_options *opt, void *str
   pl->cells = (int64_t)hbuf[1];
   pl->pair_rows = (int64_t)hbuf[2];
   pl->max_m = max_m;
+  pl->gq = b.gcp_q != nullptr;
   for (int64_t h = 0; h < b.n_haps; ++h) pl->n_max = std::max<int64_t>(pl->n_max, ho[h + 1] - ho[h]);
   pl->eps64 = std::pow(10.0, -b.gcp / 10.0);
   pl->beta64 = 1.0 - pl->eps64;
@@ -387,6 +433,10 @@ int phmm_plan_create(const phmm_batch *batch, const phmm_options *opt, void *str
   pl->beta32 = (float)pl->beta64;
   for (int m = 0; m <= PHMM_MAX_READ_LEN; ++m) {
     int c = default_cfg_of_m(std::max(m, 1));
+    if (pl->gq) {  // the kernels with per-row gap continuation exist for these groups only
+      pl->cfg_of_m[m] = gq_cfg_of_m(std::max(m, 1));
+      continue;
+    }
     if (o.bin_table_valid) {
       const int e = o.bin_rows[(std::max(m, 1) + 3) / 4];
       if (e >= 0 && e < kNumCfg32 && cfg_lanes(e) * cfg_rows(e) >= m) c = e;
@@ -403,6 +453,10 @@ int phmm_plan_create(const phmm_batch *batch, const phmm_options *opt, void *str
   {
     for (int m = 0; m <= PHMM_MAX_READ_LEN; ++m) {
       int c = bwd_default_cfg(std::max(m, 1));
+      if (pl->gq) {
+        pl->bwd_cfg_of_m[m] = gq_cfg_of_m(std::max(m, 1));
+        continue;
+      }
       if (o.bwd_table_valid) {
         const int e = o.bwd_rows[(std::max(m, 1) + 3) / 4];
         if (bwd_cfg_supported(e) && cfg_lanes(e) * cfg_rows(e) >= m) c = e;
@@ -420,6 +474,14 @@ int phmm_plan_create(const phmm_batch *batch, const phmm_options *opt, void *str
   cudaDeviceGetAttribute(&pl->sms, cudaDevAttrMultiProcessorCount, dev);
   make_layout(pl);
   pl->L.total = pl->L.bwd + bwd_workspace_bytes(pl);
+  if (kDebug) {
+    for (size_t g : bwd_guard_offsets(pl)) pl->L.guards.push_back(pl->L.bwd + g);
+    if (cudaMalloc((void **)&pl->dbg_word, 64) != cudaSuccess ||
+        cudaMemset(pl->dbg_word, 0, 64) != cudaSuccess) {
+      phmm_plan_destroy(pl);
+      return PHMM_ECUDA;
+    }
+  }
   cudaError_t ce = cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking);
   for (int i = 0; i < 7 && ce == cudaSuccess; ++i) ce = cudaEventCreate(&pl->ev[i]);
   if (ce != cudaSuccess) {
@@ -442,7 +504,10 @@ int phmm_plan_info(const phmm_plan *pl, int64_t *sum_m, int64_t *sum_n, int64_t 
 
 void phmm_plan_destroy(phmm_plan *pl) {
   if (!pl) return;
+  if (pl->dbg_word) cudaFree(pl->dbg_word);
   if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
+  if (pl->gexec_fp) cudaGraphExecDestroy(pl->gexec_fp);
+  if (pl->gexec_bp) cudaGraphExecDestroy(pl->gexec_bp);
   for (auto &e : pl->ev)
     if (e) cudaEventDestroy(e);
   if (pl->cap) cudaStreamDestroy(pl->cap);
@@ -451,12 +516,100 @@ void phmm_plan_destroy(phmm_plan *pl) {
 
 }  // extern "C"
 
+// The fused training step's calls on small batches (at most kGraphCells cells, e.g. one
+// region) replay a captured CUDA graph: their 20-30 launches would otherwise cost more than
+// the kernels.  Larger batches launch eagerly and keep the kernel-time events.  A graph is
+// captured when a call repeats the previous call's pointers (capture costs more than one
+// eager call) and replayed while they stay the same.
+constexpr int64_t kGraphCells = (int64_t)1 << 30;
+
+// Capture `enqueue` (a function of the capture stream returning a cudaError_t value) into
+// *exec; returns PHMM_OK or a status.
+template <typename F>
+static int capture_graph(phmm_plan *pl, cudaGraphExec_t *exec, F enqueue) {
+  if (*exec) {
+    cudaGraphExecDestroy(*exec);
+    *exec = nullptr;
+  }
+  CK(cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal));
+  const int rc = enqueue(pl->cap);
+  cudaGraph_t g = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(pl->cap, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc > 0 ? cuda_fail((cudaError_t)rc) : rc;
+  }
+  if (ce != cudaSuccess) return cuda_fail(ce);
+  ce = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ce != cudaSuccess) return cuda_fail(ce);
+  return PHMM_OK;
+}
+
+// ---- debug builds: guard regions and the kernels' index checks --------------------------
+struct GuardList {
+  int n;
+  unsigned long long off[64];
+};
+
+// Every byte of every guard region must still hold kGuardByte.
+__global__ void k_check_guards(const unsigned char *ws, GuardList gl, unsigned *err) {
+  unsigned bad = 0;
+  for (int g = blockIdx.x; g < gl.n; g += gridDim.x)
+    for (int k = threadIdx.x; k < (int)kGuardBytes; k += blockDim.x)
+      if (ws[gl.off[g] + k] != kGuardByte) bad = 1;
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kDbgGuard);
+}
+
+// Before a call (debug builds): fill the guard regions.
+static int dbg_begin(phmm_plan *pl, void *ws, size_t ws_bytes, void *stream) {
+  if constexpr (kDebug) {
+    if (!pl || !ws || ws_bytes < pl->L.total || ((uintptr_t)ws & 255)) return PHMM_OK;
+    for (size_t g : pl->L.guards)
+      if (cudaMemsetAsync((char *)ws + g, kGuardByte, kGuardBytes, (cudaStream_t)stream) !=
+          cudaSuccess)
+        return PHMM_ECUDA;
+  }
+  return PHMM_OK;
+}
+
+// Checks the guards now; PHMM_EGUARD if a guard or a kernel's index check failed since the
+// last check.  Waits for `stream`.
+static int dbg_check(phmm_plan *pl, void *ws, void *stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  GuardList gl;
+  gl.n = (int)std::min<size_t>(pl->L.guards.size(), 64);
+  for (int i = 0; i < gl.n; ++i) gl.off[i] = pl->L.guards[i];
+  if (gl.n > 0) k_check_guards<<<gl.n, 128, 0, s>>>((const unsigned char *)ws, gl, pl->dbg_word);
+  unsigned w = 0;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(&w, pl->dbg_word, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemsetAsync(pl->dbg_word, 0, 4, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+    return PHMM_ECUDA;
+  return w ? PHMM_EGUARD : PHMM_OK;
+}
+
+// After a call (debug builds): check the guards and the kernels' index checks.
+static int dbg_end(phmm_plan *pl, void *ws, void *stream, int rc) {
+  if (!kDebug || rc != PHMM_OK || !pl || !ws) return rc;
+  return dbg_check(pl, ws, stream);
+}
+
+// The kernels' debug fields (debug builds; otherwise no checks).
+static void dbg_args(const phmm_plan *pl, FwdArgs &a) {
+  if (!kDebug) return;
+  a.dbg_err = pl->dbg_word;
+  a.dbg_sum_m = pl->sum_m;
+  a.dbg_hcode_bytes = (int64_t)hap_code_bytes(pl->sum_n, pl->b.n_haps);
+}
+
 // Zeroed counters and the per-row parameters and codes every sweep reads.
 static int enqueue_prep(phmm_plan *pl, char *ws, cudaStream_t s, int *launches) {
   const WsLayout &L = pl->L;
   CK(cudaMemsetAsync(ws + L.zero, 0, L.zero_bytes, s));
   const int rc = launch_prep(pl->b, pl->sum_m, pl->beta32, (RowParams *)(ws + L.rp),
-                             (uint8_t *)(ws + L.rcode), (uint8_t *)(ws + L.hcode), s, launches);
+                             (uint8_t *)(ws + L.rcode), (uint8_t *)(ws + L.hcode),
+                             pl->gq ? (float2 *)(ws + L.rgap) : nullptr, s, launches);
   if (rc) return cuda_fail((cudaError_t)rc);
   return PHMM_OK;
 }
@@ -496,6 +649,8 @@ static int enqueue_forward(phmm_plan *pl, char *ws, double *out, uint8_t *flags,
   a.bq = b.base_q;
   a.iq = b.ins_q;
   a.dq = b.del_q;
+  a.gq = b.gcp_q;
+  a.rgap = pl->gq ? (const float2 *)(ws + L.rgap) : nullptr;
   a.qual_f32 = b.qual_dtype == PHMM_QUAL_F32;
   a.alpha_mode = b.alpha_mode;
   a.n_reads = b.n_reads;
@@ -514,6 +669,7 @@ static int enqueue_forward(phmm_plan *pl, char *ws, double *out, uint8_t *flags,
   a.rescue_count = rcnt;
   a.tilebuf = pl->L.tile ? (void *)(ws + L.tile) : nullptr;
   a.tile_cols = pl->n_max;
+  dbg_args(pl, a);
   const bool ext = o.first_line == PHMM_FIRST_EXT32;
   a.mode = ext ? 1 : 0;
   const int block = 32 * o.warps_per_block;
@@ -528,7 +684,7 @@ static int enqueue_forward(phmm_plan *pl, char *ws, double *out, uint8_t *flags,
         c.count_dev = grp_count + cfg;
         c.counter = (int32_t *)(ws + L.ctr32) + cfg;
         c.persistent = 1;
-        const int grid = pl->sms * std::max(1, fwd32_blocks_per_sm(cfg, ext, block));
+        const int grid = pl->sms * std::max(1, fwd32_blocks_per_sm(cfg, ext, block, pl->gq));
         rc = launch_fwd32(cfg, ext, grid, block, s, c);
         if (rc) return cuda_fail((cudaError_t)rc);
         ++launches;
@@ -569,7 +725,7 @@ static int enqueue_forward(phmm_plan *pl, char *ws, double *out, uint8_t *flags,
         for (int q = 0; q < kNumCfg64; ++q)
           c.rescue_list[q] = (int32_t *)(ws + L.xlist) + (size_t)q * std::max<int64_t>(b.n_pairs, 1);
         c.rescue_count = xcnt;
-        const int grid = pl->sms * std::max(1, fwd64_blocks_per_sm(k, tier == 1, block));
+        const int grid = pl->sms * std::max(1, fwd64_blocks_per_sm(k, tier == 1, block, pl->gq));
         rc = launch_fwd64(k, tier == 1, grid, block, s, c);
         if (rc) return cuda_fail((cudaError_t)rc);
         ++launches;
@@ -583,7 +739,7 @@ static int enqueue_forward(phmm_plan *pl, char *ws, double *out, uint8_t *flags,
 
 extern "C" {
 
-int phmm_forward(phmm_plan *pl, void *ws, size_t ws_bytes, double *out, uint8_t *flags,
+static int phmm_forward_body(phmm_plan *pl, void *ws, size_t ws_bytes, double *out, uint8_t *flags,
                  void *stream) {
   const phmm::NvtxRange nvtx("phmm_forward");
   if (!pl || !ws || (pl->b.n_pairs > 0 && (!out || !flags))) return PHMM_EINVAL;
@@ -625,70 +781,141 @@ int phmm_forward(phmm_plan *pl, void *ws, size_t ws_bytes, double *out, uint8_t 
   return rc;
 }
 
-int phmm_backward(phmm_plan *pl, void *ws, size_t ws_bytes, const double *dL, float *dbq,
-                  float *diq, float *ddq, double *dgcp, void *stream) {
+int phmm_forward(phmm_plan *pl, void *ws, size_t ws_bytes, double *out, uint8_t *flags,
+                 void *stream) {
+  int rc = dbg_begin(pl, ws, ws_bytes, stream);
+  if (rc == PHMM_OK) rc = phmm_forward_body(pl, ws, ws_bytes, out, flags, stream);
+  return dbg_end(pl, ws, stream, rc);
+}
+
+static int phmm_backward_body(phmm_plan *pl, void *ws, size_t ws_bytes, const double *dL, float *dbq,
+                  float *diq, float *ddq, float *dgq, double *dgcp, void *stream) {
   const phmm::NvtxRange nvtx("phmm_backward");
   if (!pl || !ws || !dgcp) return PHMM_EINVAL;
-  if (pl->sum_m > 0 && (!dbq || !diq || !ddq)) return PHMM_EINVAL;
+  if (pl->sum_m > 0 && (!dbq || !diq || !ddq || (pl->gq && !dgq))) return PHMM_EINVAL;
   if (pl->b.n_pairs > 0 && !dL) return PHMM_EINVAL;
   if (((uintptr_t)ws & 255) != 0) return PHMM_EINVAL;
   if (ws_bytes < pl->L.total) return PHMM_ENOMEM;
-  if (pl->max_m > PHMM_MAX_READ_LEN) return PHMM_ETOOLONG;  // row tiles have no adjoint
   if (!pl->fwd_done) return PHMM_ESTATE;
   (void)cudaGetLastError();
   int launches = 0;
   pl->bwd_timed = false;
   pl->partials_done = false;  // the sweep overwrites the partials with scaled ones
   pl->red_from = 4;
-  int rc = bwd_enqueue_impl(pl, (char *)ws, dL, dbq, diq, ddq, dgcp, (cudaStream_t)stream,
-                            &launches, pl->ev + 3);
+  int rc = bwd_enqueue_impl(pl, (char *)ws, dL, dbq, diq, ddq, pl->gq ? dgq : nullptr, dgcp,
+                            (cudaStream_t)stream, &launches, pl->ev + 3);
   pl->launches_bwd = launches;
   if (rc) return cuda_fail((cudaError_t)rc);
   pl->bwd_timed = true;
   return PHMM_OK;
 }
 
-int phmm_forward_partials(phmm_plan *pl, void *ws, size_t ws_bytes, double *out,
+int phmm_backward(phmm_plan *pl, void *ws, size_t ws_bytes, const double *dL, float *dbq,
+                  float *diq, float *ddq, float *dgq, double *dgcp, void *stream) {
+  int rc = dbg_begin(pl, ws, ws_bytes, stream);
+  if (rc == PHMM_OK) rc = phmm_backward_body(pl, ws, ws_bytes, dL, dbq, diq, ddq, dgq, dgcp, stream);
+  return dbg_end(pl, ws, stream, rc);
+}
+
+static int phmm_forward_partials_body(phmm_plan *pl, void *ws, size_t ws_bytes, double *out,
                           uint8_t *flags, void *stream) {
   const phmm::NvtxRange nvtx("phmm_forward_partials");
   if (!pl || !ws || (pl->b.n_pairs > 0 && (!out || !flags))) return PHMM_EINVAL;
   if (((uintptr_t)ws & 255) != 0) return PHMM_EINVAL;
   if (ws_bytes < pl->L.total) return PHMM_ENOMEM;
-  if (pl->max_m > PHMM_MAX_READ_LEN) return PHMM_ETOOLONG;
   cudaStream_t s = (cudaStream_t)stream;
   (void)cudaGetLastError();
   pl->bwd_timed = false;
   pl->partials_done = false;
-  int launches = 0;
-  int rc = enqueue_prep(pl, (char *)ws, s, &launches);
-  if (rc) return rc;
-  rc = bwd_sweep_impl(pl, (char *)ws, nullptr, out, flags, s, &launches, pl->ev + 3);
-  pl->launches_fwd = launches;
-  if (rc) return cuda_fail((cudaError_t)rc);
+  const void *key_fp[3] = {ws, out, flags};
+  const bool repeat_fp = std::memcmp(key_fp, pl->gfp_prev, sizeof(key_fp)) == 0;
+  std::memcpy(pl->gfp_prev, key_fp, sizeof(key_fp));
+  const bool replay_fp = pl->gexec_fp && std::memcmp(key_fp, pl->gfp_key, sizeof(key_fp)) == 0;
+  if (pl->o.use_graph && pl->cells <= kGraphCells && (replay_fp || repeat_fp)) {
+    const void *(&key)[3] = key_fp;
+    if (!replay_fp) {
+      int n = 0;
+      const int rc = capture_graph(pl, &pl->gexec_fp, [&](cudaStream_t cs) {
+        int r = enqueue_prep(pl, (char *)ws, cs, &n);
+        if (r) return r;
+        return bwd_sweep_impl(pl, (char *)ws, nullptr, out, flags, cs, &n, pl->ev + 3);
+      });
+      if (rc) return rc;
+      std::memcpy(pl->gfp_key, key, sizeof(key));
+      pl->gfp_launches = n;
+    }
+    CK(cudaGraphLaunch(pl->gexec_fp, s));
+    pl->launches_fwd = pl->gfp_launches;
+  } else {
+    int launches = 0;
+    int rc = enqueue_prep(pl, (char *)ws, s, &launches);
+    if (rc) return rc;
+    rc = bwd_sweep_impl(pl, (char *)ws, nullptr, out, flags, s, &launches, pl->ev + 3);
+    pl->launches_fwd = launches;
+    if (rc) return cuda_fail((cudaError_t)rc);
+  }
   pl->fwd_done = true;
   pl->partials_done = true;
   return PHMM_OK;
 }
 
-int phmm_backward_partials(phmm_plan *pl, void *ws, size_t ws_bytes, const double *dL,
-                           float *dbq, float *diq, float *ddq, double *dgcp, void *stream) {
+int phmm_forward_partials(phmm_plan *pl, void *ws, size_t ws_bytes, double *out,
+                          uint8_t *flags, void *stream) {
+  int rc = dbg_begin(pl, ws, ws_bytes, stream);
+  if (rc == PHMM_OK) rc = phmm_forward_partials_body(pl, ws, ws_bytes, out, flags, stream);
+  return dbg_end(pl, ws, stream, rc);
+}
+
+static int phmm_backward_partials_body(phmm_plan *pl, void *ws, size_t ws_bytes, const double *dL,
+                           float *dbq, float *diq, float *ddq, float *dgq, double *dgcp,
+                           void *stream) {
   const phmm::NvtxRange nvtx("phmm_backward_partials");
   if (!pl || !ws || !dgcp) return PHMM_EINVAL;
-  if (pl->sum_m > 0 && (!dbq || !diq || !ddq)) return PHMM_EINVAL;
+  if (pl->sum_m > 0 && (!dbq || !diq || !ddq || (pl->gq && !dgq))) return PHMM_EINVAL;
   if (pl->b.n_pairs > 0 && !dL) return PHMM_EINVAL;
   if (((uintptr_t)ws & 255) != 0) return PHMM_EINVAL;
   if (ws_bytes < pl->L.total) return PHMM_ENOMEM;
   if (!pl->partials_done) return PHMM_ESTATE;
   cudaStream_t s = (cudaStream_t)stream;
   (void)cudaGetLastError();
+  float *gq = pl->gq ? dgq : nullptr;
+  const void *key_bp[7] = {ws, dL, dbq, diq, ddq, gq, dgcp};
+  const bool repeat_bp = std::memcmp(key_bp, pl->gbp_prev, sizeof(key_bp)) == 0;
+  std::memcpy(pl->gbp_prev, key_bp, sizeof(key_bp));
+  const bool replay_bp = pl->gexec_bp && std::memcmp(key_bp, pl->gbp_key, sizeof(key_bp)) == 0;
+  if (pl->o.use_graph && pl->cells <= kGraphCells && (replay_bp || repeat_bp)) {
+    const void *(&key)[7] = key_bp;
+    if (!replay_bp) {
+      int n = 0;
+      const int rc = capture_graph(pl, &pl->gexec_bp, [&](cudaStream_t cs) {
+        return bwd_reduce_impl(pl, (char *)ws, dL, dbq, diq, ddq, gq, dgcp, cs, &n, pl->ev[5]);
+      });
+      if (rc) return rc;
+      std::memcpy(pl->gbp_key, key, sizeof(key));
+      pl->gbp_launches = n;
+    }
+    CK(cudaGraphLaunch(pl->gexec_bp, s));
+    pl->launches_bwd = pl->gbp_launches;
+    pl->bwd_timed = false;  // kernel times are recorded by eager calls only
+    return PHMM_OK;
+  }
   int launches = 0;
   pl->red_from = 6;
   CK(cudaEventRecord(pl->ev[6], s));
-  const int rc = bwd_reduce_impl(pl, (char *)ws, dL, dbq, diq, ddq, dgcp, s, &launches, pl->ev[5]);
+  const int rc = bwd_reduce_impl(pl, (char *)ws, dL, dbq, diq, ddq, gq, dgcp, s, &launches,
+                                 pl->ev[5]);
   pl->launches_bwd = launches;
   if (rc) return cuda_fail((cudaError_t)rc);
   pl->bwd_timed = true;
   return PHMM_OK;
+}
+
+int phmm_backward_partials(phmm_plan *pl, void *ws, size_t ws_bytes, const double *dL,
+                           float *dbq, float *diq, float *ddq, float *dgq, double *dgcp,
+                           void *stream) {
+  int rc = dbg_begin(pl, ws, ws_bytes, stream);
+  if (rc == PHMM_OK) rc = phmm_backward_partials_body(pl, ws, ws_bytes, dL, dbq, diq, ddq, dgq, dgcp, stream);
+  return dbg_end(pl, ws, stream, rc);
 }
 
 int phmm_plan_launch_count(const phmm_plan *pl, int which) {
@@ -747,6 +974,23 @@ int phmm_plan_backward_ms(phmm_plan *pl, float *ms_adjoint, float *ms_reduce) {
 
 }  // extern "C"
 
+extern "C" {
+
+int phmm_debug_guard_offset(const phmm_plan *pl, int k, size_t *offset) {
+  if (!kDebug) return PHMM_ESTATE;
+  if (!pl || !offset || k < 0 || k >= (int)pl->L.guards.size()) return PHMM_EINVAL;
+  *offset = pl->L.guards[k];
+  return PHMM_OK;
+}
+
+int phmm_debug_check(phmm_plan *pl, void *ws, void *stream) {
+  if (!kDebug) return PHMM_ESTATE;
+  if (!pl || !ws) return PHMM_EINVAL;
+  return dbg_check(pl, ws, stream);
+}
+
+}  // extern "C"
+
 // Accessors used by the backward translation unit.
 namespace phmm {
 const phmm_batch &plan_batch(const phmm_plan *pl) { return pl->b; }
@@ -761,6 +1005,13 @@ size_t plan_layout_hcode(const phmm_plan *pl) { return pl->L.hcode; }
 double plan_eps64(const phmm_plan *pl) { return pl->eps64; }
 int64_t plan_n_max(const phmm_plan *pl) { return pl->n_max; }
 int64_t plan_pair_rows(const phmm_plan *pl) { return pl->pair_rows; }
+int plan_max_m(const phmm_plan *pl) { return pl->max_m; }
+bool plan_gq(const phmm_plan *pl) { return pl->gq; }
+unsigned *plan_dbg_word(const phmm_plan *pl) { return kDebug ? pl->dbg_word : nullptr; }
+int64_t plan_hcode_bytes(const phmm_plan *pl) {
+  return (int64_t)hap_code_bytes(pl->sum_n, pl->b.n_haps);
+}
+size_t plan_layout_rgap(const phmm_plan *pl) { return pl->L.rgap; }
 const int *plan_bwd_cfg_of_m(const phmm_plan *pl) { return pl->bwd_cfg_of_m; }
 const std::vector<int> &plan_bwd_used(const phmm_plan *pl) { return pl->bwd_used; }
 // 0 counts, 1 key, 2 offsets, 3 cursor, 4 grp_begin, 5 grp_count, 6 order, 7 ctr32,

@@ -27,5 +27,8 @@ FwdKernel fwd32_plain_hi(int L, int K);  // L in {16, 32}
 FwdKernel fwd32_ext_lo(int L, int K);
 FwdKernel fwd32_ext_hi(int L, int K);
 FwdKernel fwd64_table(int K, bool ext);  // L = 32, K in {4, 8, 16}
+// per-base gap-continuation track: extended FP32 groups of the track's table, FP64 tiers
+FwdKernel fwd32_gq(int L, int K);
+FwdKernel fwd64_gq(int K, bool ext);
 
 }  // namespace phmm

@@ -122,17 +122,19 @@ __global__ void k_segment_sort(const int64_t *seg_off, int64_t R, const int32_t 
 
 // One warp per read: FP64 sum of the partials of its pairs, in pair order, each times
 // dL[pair] when dL is given (partials of log10 L itself), else as stored (already scaled).
+// part_gq / dgq: the per-base gap-continuation partials (null without a track).
 __global__ void k_read_reduce(const int64_t *read_off, int64_t R, const int64_t *seg_off,
                               const int32_t *sorted, const int64_t *poff, const float *part_bq,
-                              const float *part_iq, const float *part_dq, const double *dL,
-                              float *dbq, float *diq, float *ddq) {
+                              const float *part_iq, const float *part_dq, const float *part_gq,
+                              const double *dL, float *dbq, float *diq, float *ddq,
+                              float *dgq) {
   const int lane = threadIdx.x & 31;
   for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < R;
        r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const int64_t r0 = read_off[r], m = read_off[r + 1] - r0;
     const int64_t b = seg_off[r], e = seg_off[r + 1];
     for (int64_t i = lane; i < m; i += 32) {
-      double sb = 0.0, si = 0.0, sd = 0.0;
+      double sb = 0.0, si = 0.0, sd = 0.0, sg = 0.0;
       for (int64_t k = b; k < e; ++k) {
         const int32_t pr = sorted[k];
         const int64_t o = poff[pr] + i;
@@ -140,10 +142,12 @@ __global__ void k_read_reduce(const int64_t *read_off, int64_t R, const int64_t 
         sb += w * (double)part_bq[o];
         si += w * (double)part_iq[o];
         sd += w * (double)part_dq[o];
+        if (part_gq) sg += w * (double)part_gq[o];
       }
       dbq[r0 + i] = (float)sb;
       diq[r0 + i] = (float)si;
       ddq[r0 + i] = (float)sd;
+      if (dgq) dgq[r0 + i] = (float)sg;
     }
   }
 }
@@ -239,9 +243,9 @@ int pair_offsets(const phmm_batch &b, char *scratch, int64_t **poff, cudaStream_
 // Per-read FP64 reduction of the pair partials and the FP64 sum of per-pair d/dgcp; with
 // dL non-null the per-pair values are partials of log10 L, weighted by dL[p] in FP64.
 int reduce_gradients(const phmm_batch &b, char *scratch, const float *part_bq,
-                     const float *part_iq, const float *part_dq, const double *pair_dgcp,
-                     const double *dL, float *dbq, float *diq, float *ddq, double *dgcp,
-                     cudaStream_t s, int *launches) {
+                     const float *part_iq, const float *part_dq, const float *part_gq,
+                     const double *pair_dgcp, const double *dL, float *dbq, float *diq,
+                     float *ddq, float *dgq, double *dgcp, cudaStream_t s, int *launches) {
   ReduceScratch rs = carve(scratch, b.n_pairs, b.n_reads);
   const int64_t P = b.n_pairs, R = b.n_reads;
   cudaMemsetAsync(rs.cnt, 0, 8 * (size_t)(R + 1), s);
@@ -255,8 +259,8 @@ int reduce_gradients(const phmm_batch &b, char *scratch, const float *part_bq,
     k_segment_sort<<<grid_for(R * 32, 256), 256, 0, s>>>(rs.seg_off, R, rs.seg, rs.sorted);
   }
   k_read_reduce<<<grid_for(R * 32, 256), 256, 0, s>>>(b.read_off, R, rs.seg_off, rs.sorted,
-                                                      rs.poff, part_bq, part_iq, part_dq, dL,
-                                                      dbq, diq, ddq);
+                                                      rs.poff, part_bq, part_iq, part_dq,
+                                                      part_gq, dL, dbq, diq, ddq, dgq);
   k_sum_stage1<<<kSumBlocks, 256, 0, s>>>(pair_dgcp, dL, P, rs.sum_part);
   k_sum_stage2<<<1, 256, 0, s>>>(rs.sum_part, dgcp);
   *launches += 8;

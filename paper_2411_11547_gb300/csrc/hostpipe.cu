@@ -53,6 +53,7 @@ struct HostOut {
   uint8_t *flags;
   float *gb, *gi, *gd;
   double *gg;
+  float *gq;  // per-base gap-continuation gradients (batches with a track), else null
 };
 
 // memcpy split over host threads (large copies only)
@@ -114,8 +115,9 @@ int drain(Slot &sl, const HostOut &o) {
     par_copy(o.gb + sl.b0, g, gbytes);
     par_copy(o.gi + sl.b0, g + up(gbytes), gbytes);
     par_copy(o.gd + sl.b0, g + 2 * up(gbytes), gbytes);
+    if (o.gq) par_copy(o.gq + sl.b0, g + 3 * up(gbytes), gbytes);
     double gg;
-    std::memcpy(&gg, g + 3 * up(gbytes), 8);
+    std::memcpy(&gg, g + (o.gq ? 4 : 3) * up(gbytes), 8);
     *o.gg += gg;
   }
   phmm_plan_destroy(sl.plan);
@@ -183,6 +185,10 @@ static int host_pipeline(const phmm_batch *hb, const phmm_options *opt, int64_t 
       !b.hap_off || (b.n_pairs > 0 && (!b.pair_read || !b.pair_hap)))
     return PHMM_EINVAL;
   if (grad && (!ho_.gb || !ho_.gi || !ho_.gd || !ho_.gg)) return PHMM_EINVAL;
+  const bool gqt = b.gcp_q != nullptr;  // per-base gap-continuation track
+  if (grad && gqt && !ho_.gq) return PHMM_EINVAL;
+  HostOut hout = ho_;
+  if (!gqt) hout.gq = nullptr;
   const int64_t R = b.n_reads, H = b.n_haps, P = b.n_pairs;
   const int64_t *ro = b.read_off, *ho = b.hap_off;
   if (ro[0] != 0 || ho[0] != 0) return PHMM_EINVAL;
@@ -196,6 +202,7 @@ static int host_pipeline(const phmm_batch *hb, const phmm_options *opt, int64_t 
     std::memset(ho_.gb, 0, sm_all);
     std::memset(ho_.gi, 0, sm_all);
     std::memset(ho_.gd, 0, sm_all);
+    if (gqt) std::memset(ho_.gq, 0, sm_all);
   }
   if (P == 0) return PHMM_OK;
   // pairs grouped by read: already so when pair_read is non-decreasing (all-vs-all batches
@@ -277,7 +284,7 @@ static int host_pipeline(const phmm_batch *hb, const phmm_options *opt, int64_t 
     }
     left -= cells;
     Slot &sl = slot[k & 1];
-    if ((rc = drain(sl, ho_))) break;
+    if ((rc = drain(sl, hout))) break;
     // the subset's pairs and haplotypes.  Fast path: the pairs are one contiguous range and
     // the haplotypes they use fill most of one contiguous range [hmin, hmax], which is then
     // copied whole and renumbered by offset; otherwise haplotypes are renumbered in
@@ -312,14 +319,14 @@ static int host_pipeline(const phmm_batch *hb, const phmm_options *opt, int64_t 
     const int64_t nh = hrange ? (int64_t)(hmax - hmin + 1) : (int64_t)haps.size();
     const int64_t sm = ro[hi] - ro[lo];
     // packed layout: bases, 3 quals, read offsets, haplotype bases and offsets, pair ids,
-    // and (gradient mode) the pairs' dL
-    size_t off[10], tot = 0;
+    // (gradient mode) the pairs' dL, and the gap-continuation track
+    size_t off[11], tot = 0;
     const size_t rb = direct ? 0 : (size_t)sm;           // read bases / quals staged
     const size_t hb = direct && hrange ? 0 : (size_t)sn;   // haplotype bases staged
-    const size_t sz[10] = {rb, rb * qe, rb * qe, rb * qe, (size_t)(nr + 1) * 8, hb,
+    const size_t sz[11] = {rb, rb * qe, rb * qe, rb * qe, (size_t)(nr + 1) * 8, hb,
                            (size_t)(nh + 1) * 8, (size_t)np * 4, (size_t)np * 4,
-                           grad ? (size_t)np * 8 : 0};
-    for (int i = 0; i < 10; ++i) {
+                           grad ? (size_t)np * 8 : 0, gqt ? rb * qe : 0};
+    for (int i = 0; i < 11; ++i) {
       off[i] = tot;
       tot += up(sz[i]);
     }
@@ -328,7 +335,7 @@ static int host_pipeline(const phmm_batch *hb, const phmm_options *opt, int64_t 
     sl.sm = sm;
     // results: log10 L, flags, and (gradient mode) the three per-base gradients and d/dgcp
     sl.grad_off = up(8 * (size_t)np) + up((size_t)np);
-    const size_t res = sl.grad_off + (grad ? 3 * up(4 * (size_t)sm) + up(8) : 0);
+    const size_t res = sl.grad_off + (grad ? (gqt ? 4 : 3) * up(4 * (size_t)sm) + up(8) : 0);
     if ((rc = grow_pinned(&sl.stage, &sl.stage_cap, tot))) break;
     if ((rc = grow_pinned(&sl.hres, &sl.hres_cap, res))) break;
     if ((rc = grow_device((void **)&sl.dev, &sl.dev_cap, tot + res))) break;
@@ -338,6 +345,7 @@ static int host_pipeline(const phmm_batch *hb, const phmm_options *opt, int64_t 
       par_copy(st + off[1], (const unsigned char *)b.base_q + ro[lo] * qe, sm * qe);
       par_copy(st + off[2], (const unsigned char *)b.ins_q + ro[lo] * qe, sm * qe);
       par_copy(st + off[3], (const unsigned char *)b.del_q + ro[lo] * qe, sm * qe);
+      if (gqt) par_copy(st + off[10], (const unsigned char *)b.gcp_q + ro[lo] * qe, sm * qe);
     }
     int64_t *sro = (int64_t *)(st + off[4]);
     for (int64_t r = 0; r <= nr; ++r) sro[r] = ro[lo + r] - ro[lo];
@@ -378,11 +386,13 @@ static int host_pipeline(const phmm_batch *hb, const phmm_options *opt, int64_t 
       d.base_q = (const unsigned char *)b.base_q + ro[lo] * qe;
       d.ins_q = (const unsigned char *)b.ins_q + ro[lo] * qe;
       d.del_q = (const unsigned char *)b.del_q + ro[lo] * qe;
+      if (gqt) d.gcp_q = (const unsigned char *)b.gcp_q + ro[lo] * qe;
     } else {
       d.read_bases = sl.dev + off[0];
       d.base_q = sl.dev + off[1];
       d.ins_q = sl.dev + off[2];
       d.del_q = sl.dev + off[3];
+      if (gqt) d.gcp_q = sl.dev + off[10];
     }
     d.read_off = (const int64_t *)(sl.dev + off[4]);
     d.hap_bases = direct && hrange ? b.hap_bases + ho[hmin] : sl.dev + off[5];
@@ -401,8 +411,9 @@ static int host_pipeline(const phmm_batch *hb, const phmm_options *opt, int64_t 
       if ((rc = phmm_forward_partials(sl.plan, sl.ws, wsb, dout, dfl, sl.s))) break;
       if ((rc = phmm_backward_partials(sl.plan, sl.ws, wsb, (const double *)(sl.dev + off[9]),
                                        (float *)g, (float *)(g + gbytes),
-                                       (float *)(g + 2 * gbytes), (double *)(g + 3 * gbytes),
-                                       sl.s)))
+                                       (float *)(g + 2 * gbytes),
+                                       gqt ? (float *)(g + 3 * gbytes) : nullptr,
+                                       (double *)(g + (gqt ? 4 : 3) * gbytes), sl.s)))
         break;
     } else {
       if ((rc = phmm_forward(sl.plan, sl.ws, wsb, dout, dfl, sl.s))) break;
@@ -417,7 +428,7 @@ static int host_pipeline(const phmm_batch *hb, const phmm_options *opt, int64_t 
     ++k;
   }
   for (auto &sl : slot) {
-    const int r2 = rc ? (cudaStreamSynchronize(sl.s), 0) : drain(sl, ho_);
+    const int r2 = rc ? (cudaStreamSynchronize(sl.s), 0) : drain(sl, hout);
     if (!rc) rc = r2;
     if (sl.plan) phmm_plan_destroy(sl.plan);
     sl.plan = nullptr;
@@ -434,15 +445,15 @@ extern "C" int phmm_score_host(const phmm_batch *hb, const phmm_options *opt,
                                int64_t subset_cells, double *out_log10, uint8_t *out_flags) {
   const phmm::NvtxRange nvtx("phmm_score_host");
   return host_pipeline(hb, opt, subset_cells, nullptr,
-                       HostOut{out_log10, out_flags, nullptr, nullptr, nullptr, nullptr});
+                       HostOut{out_log10, out_flags, nullptr, nullptr, nullptr, nullptr, nullptr});
 }
 
 extern "C" int phmm_grad_host(const phmm_batch *hb, const phmm_options *opt,
                               int64_t subset_cells, const double *dL, double *out_log10,
                               uint8_t *out_flags, float *d_base_q, float *d_ins_q,
-                              float *d_del_q, double *d_gcp) {
+                              float *d_del_q, float *d_gcp_q, double *d_gcp) {
   const phmm::NvtxRange nvtx("phmm_grad_host");
   if (!dL) return PHMM_EINVAL;
   return host_pipeline(hb, opt, subset_cells, dL,
-                       HostOut{out_log10, out_flags, d_base_q, d_ins_q, d_del_q, d_gcp});
+                       HostOut{out_log10, out_flags, d_base_q, d_ins_q, d_del_q, d_gcp, d_gcp_q});
 }

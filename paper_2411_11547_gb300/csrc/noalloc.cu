@@ -15,7 +15,7 @@
 
 namespace phmm {
 int launch_prep(const phmm_batch &b, int64_t sum_m, float beta32, RowParams *rp,
-                uint8_t *rcode, uint8_t *hcode, cudaStream_t s, int *launches);
+                uint8_t *rcode, uint8_t *hcode, float2 *rgap, cudaStream_t s, int *launches);
 int launch_fwd32(int cfg, bool ext, int grid, int block, cudaStream_t s, const FwdArgs &a);
 }  // namespace phmm
 
@@ -87,6 +87,7 @@ extern "C" int phmm_forward_noalloc(const phmm_batch *batch, double *out_log10,
   if (b.qual_dtype != PHMM_QUAL_U8 && b.qual_dtype != PHMM_QUAL_F32) return PHMM_EINVAL;
   if (b.alpha_mode != 0 && b.alpha_mode != 1) return PHMM_EINVAL;
   if (!(b.gcp > 0.0) || !(b.gcp < 1e300)) return PHMM_EINVAL;
+  if (b.gcp_q) return PHMM_EINVAL;  // scalar gap continuation only
   cudaStream_t s = (cudaStream_t)stream;
 
   // set-up, once per device: the device address of the static scratch
@@ -134,7 +135,7 @@ extern "C" int phmm_forward_noalloc(const phmm_batch *batch, double *out_log10,
 
   const double eps64 = pow(10.0, -b.gcp / 10.0);
   int launches = 0;
-  if (launch_prep(b, sum_m, (float)(1.0 - eps64), rp, rcode, hcode, s, &launches) != 0)
+  if (launch_prep(b, sum_m, (float)(1.0 - eps64), rp, rcode, hcode, nullptr, s, &launches) != 0)
     return PHMM_ECUDA;
   if (b.n_pairs == 0) return PHMM_OK;
 

@@ -55,6 +55,8 @@ struct FwdArgs {
   const uint8_t *rcode;     // read base codes per read position
   const uint8_t *hcode;     // haplotype codes, each haplotype 16-byte aligned, NULLC padded
   const void *bq, *iq, *dq; // raw Phred inputs (FP64 path derives its own parameters)
+  const void *gq;           // raw per-base gap-continuation Phred values, or null
+  const float2 *rgap;       // FP32 (eps_i, beta_i) per read position (plans with a track)
   int32_t qual_f32, alpha_mode;
   int64_t n_reads, n_haps;
   const int32_t *list;      // pair ids to process (nullptr: identity 0..count-1)
@@ -74,7 +76,14 @@ struct FwdArgs {
   int32_t rescue;           // 1: append failures to rescue lists, 0: write whatever results
   void *tilebuf;            // row tiles: 2 x tile_cols TileCol<T> per resident warp (or null)
   int64_t tile_cols;        // columns per tile buffer (the longest haplotype)
+  // debug builds (PHMM_DEBUG): the sizes the kernels check their indexes against, and the
+  // word they report a failed check in (null: no checks)
+  unsigned *dbg_err;
+  int64_t dbg_sum_m, dbg_hcode_bytes, dbg_nslots;
 };
+
+// Bits of the debug word (PHMM_DEBUG builds).
+constexpr unsigned kDbgGuard = 1u, kDbgPairIndex = 4u, kDbgSlot = 8u, kDbgCheckpoints = 16u;
 
 // Host-side NVTX range over a library call (profilers show the calls on their timelines;
 // the markers cost nothing without a tool attached).
@@ -90,7 +99,16 @@ int launch_fwd32(int cfg, bool ext, int grid, int block, cudaStream_t s, const F
 int launch_fwd64(int cfg64, bool ext, int grid, int block, cudaStream_t s, const FwdArgs &a);
 size_t fwd32_smem(int cfg, int block);
 size_t fwd64_smem(int cfg64, int block);
-int fwd32_blocks_per_sm(int cfg, bool ext, int block);
-int fwd64_blocks_per_sm(int cfg64, bool ext, int block);
+int fwd32_blocks_per_sm(int cfg, bool ext, int block, bool gq = false);
+int fwd64_blocks_per_sm(int cfg64, bool ext, int block, bool gq = false);
+
+// Read length -> group of a plan with a per-base gap-continuation track (the kernels with
+// per-row gap continuation are built for these groups only).
+__host__ __device__ constexpr int gq_cfg_of_m(int m) {
+  return m <= 64 ? cfg_index(16, 4)
+                 : (m <= 128 ? cfg_index(16, 8)
+                             : (m <= 256 ? cfg_index(32, 8)
+                                         : (m <= 384 ? cfg_index(32, 12) : cfg_index(32, 16))));
+}
 
 }  // namespace phmm

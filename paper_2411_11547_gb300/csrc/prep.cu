@@ -26,15 +26,17 @@ __device__ __forceinline__ int base_code(uint8_t b) {
 }
 
 // Error bits of the validation word.
-constexpr unsigned kErrBase = 1u, kErrQual = 2u, kErrPair = 4u, kErrAlpha = 8u;
+constexpr unsigned kErrBase = 1u, kErrQual = 2u, kErrPair = 4u, kErrAlpha = 8u, kErrGcp = 16u;
 
 __global__ void k_validate_reads(const uint8_t *bases, const void *bq, const void *iq,
-                                 const void *dq, int qual_f32, int alpha_mode, int64_t total,
-                                 unsigned *err) {
+                                 const void *dq, const void *gq, int qual_f32, int alpha_mode,
+                                 int64_t total, unsigned *err) {
   unsigned e = 0;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
        g += (int64_t)gridDim.x * blockDim.x) {
     if (base_code(bases[g]) < 0) e |= kErrBase;
+    // a per-base gap-continuation value must leave eps < 1 (beta > 0)
+    if (gq && !(qual_at(gq, qual_f32, g) > 0.0)) e |= kErrGcp;
     // uint8 and float32 Phred values are exact in float
     const float b = (float)qual_at(bq, qual_f32, g), i = (float)qual_at(iq, qual_f32, g),
                 d = (float)qual_at(dq, qual_f32, g);
@@ -82,10 +84,13 @@ __global__ void k_validate_pairs(const int32_t *pr, const int32_t *ph, int64_t P
   if ((threadIdx.x & 31) == 0 && rows) atomicAdd(cells + 1, rows);
 }
 
-// Per read position: code + (alpha/beta, delta, zeta, Q) in FP32.
+// Per read position: code + (alpha/beta, delta, zeta, Q) in FP32; with a per-base
+// gap-continuation track also (eps_i, beta_i), each rounded from FP64 as the scalar eps and
+// beta are (so a uniform track gives the scalar path's parameters exactly).
 __global__ void k_prep_reads(const uint8_t *bases, const void *bq, const void *iq,
-                             const void *dq, int qual_f32, int alpha_mode, int64_t total,
-                             float beta, RowParams *rp, uint8_t *rcode) {
+                             const void *dq, const void *gq, int qual_f32, int alpha_mode,
+                             int64_t total, float beta, RowParams *rp, uint8_t *rcode,
+                             float2 *rgap) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
        g += (int64_t)gridDim.x * blockDim.x) {
     const int c = base_code(bases[g]);
@@ -94,7 +99,13 @@ __global__ void k_prep_reads(const uint8_t *bases, const void *bq, const void *i
                 d = (float)qual_at(dq, qual_f32, g);
     const float Q = exp10f(-b * 0.1f), dl = exp10f(-i * 0.1f), zt = exp10f(-d * 0.1f);
     const float al = alpha_mode ? 1.f - exp10f(-(i + d) * 0.1f) : 1.f - (dl + zt);
-    rp[g] = make_float4(al / beta, dl, zt, Q);
+    float be = beta;
+    if (gq) {
+      const double e64 = pow(10.0, -qual_at(gq, qual_f32, g) / 10.0);
+      be = (float)(1.0 - e64);
+      rgap[g] = make_float2((float)e64, be);
+    }
+    rp[g] = make_float4(al / be, dl, zt, Q);
   }
 }
 
@@ -215,8 +226,8 @@ int launch_validate(const phmm_batch &b, int64_t sum_m, int64_t sum_n, unsigned 
                     unsigned long long *cells, cudaStream_t s) {
   if (sum_m > 0)
     k_validate_reads<<<grid_for(sum_m, 256), 256, 0, s>>>(
-        b.read_bases, b.base_q, b.ins_q, b.del_q, b.qual_dtype == PHMM_QUAL_F32, b.alpha_mode,
-        sum_m, err);
+        b.read_bases, b.base_q, b.ins_q, b.del_q, b.gcp_q, b.qual_dtype == PHMM_QUAL_F32,
+        b.alpha_mode, sum_m, err);
   if (sum_n > 0) k_validate_haps<<<grid_for(sum_n, 256), 256, 0, s>>>(b.hap_bases, sum_n, err);
   if (b.n_pairs > 0)
     k_validate_pairs<<<grid_for(b.n_pairs, 256), 256, 0, s>>>(
@@ -226,11 +237,11 @@ int launch_validate(const phmm_batch &b, int64_t sum_m, int64_t sum_n, unsigned 
 }
 
 int launch_prep(const phmm_batch &b, int64_t sum_m, float beta32, RowParams *rp,
-                uint8_t *rcode, uint8_t *hcode, cudaStream_t s, int *launches) {
+                uint8_t *rcode, uint8_t *hcode, float2 *rgap, cudaStream_t s, int *launches) {
   if (sum_m > 0) {
-    k_prep_reads<<<grid_for(sum_m, 256), 256, 0, s>>>(b.read_bases, b.base_q, b.ins_q, b.del_q,
-                                                      b.qual_dtype == PHMM_QUAL_F32,
-                                                      b.alpha_mode, sum_m, beta32, rp, rcode);
+    k_prep_reads<<<grid_for(sum_m, 256), 256, 0, s>>>(
+        b.read_bases, b.base_q, b.ins_q, b.del_q, b.gcp_q, b.qual_dtype == PHMM_QUAL_F32,
+        b.alpha_mode, sum_m, beta32, rp, rcode, rgap);
     ++*launches;
   }
   k_prep_haps<<<grid_for(b.n_haps * 32, 256), 256, 0, s>>>(b.hap_bases, b.hap_off, b.n_haps,

@@ -191,7 +191,7 @@ static float time_candidate(const SubBatch &sb, const phmm_options &opt, int whi
     double *gg = (double *)(((uintptr_t)(gd + sm) + 7) & ~(uintptr_t)7);
     auto run = [&]() {
       if (which == 1) return phmm_forward(plan, w, wsb, (double *)out, (uint8_t *)flags, s);
-      return phmm_backward(plan, w, wsb, (const double *)dL, gb, gi, gd, gg, s);
+      return phmm_backward(plan, w, wsb, (const double *)dL, gb, gi, gd, nullptr, gg, s);
     };
     ok = ok && phmm_forward(plan, w, wsb, (double *)out, (uint8_t *)flags, s) == PHMM_OK &&
          run() == PHMM_OK;  // warm-up (graph capture, caches)
@@ -230,6 +230,8 @@ extern "C" int phmm_autotune(const phmm_batch *batch, phmm_options *opt, int whi
     if (rc != PHMM_OK) return rc;
     phmm_plan_destroy(pl);
   }
+  // a batch with a per-base gap-continuation track runs a fixed group table: nothing to tune
+  if (b.gcp_q) return PHMM_OK;
   if (b.n_pairs == 0) return PHMM_OK;
   std::vector<int64_t> ro(b.n_reads + 1), ho(b.n_haps + 1);
   std::vector<int32_t> pr(b.n_pairs), ph(b.n_pairs);

@@ -134,10 +134,12 @@ __device__ __forceinline__ double qual_at(const void *q, int f32, int64_t g) {
              : (double)reinterpret_cast<const uint8_t *>(q)[g];
 }
 
-// Row parameters of read position g: alpha' = alpha/beta, delta, zeta, Q.
+// Row parameters of read position g: alpha' = alpha/beta, delta, zeta, Q.  be: the row's
+// beta when the batch has a per-base gap-continuation track (FP64; the FP32 parameters were
+// prepared with it), else 0 for the scalar beta.
 template <typename T>
 __device__ __forceinline__ void row_params(const FwdArgs &a, int64_t g, T &ap, T &dl, T &zt,
-                                           T &Q) {
+                                           T &Q, double be = 0.0) {
   if constexpr (sizeof(T) == 4) {
     RowParams v = a.rp[g];
     ap = v.x;
@@ -151,7 +153,21 @@ __device__ __forceinline__ void row_params(const FwdArgs &a, int64_t g, T &ap, T
     dl = exp10(-iq / 10.0);
     zt = exp10(-dq / 10.0);
     const double al = a.alpha_mode ? 1.0 - exp10(-(iq + dq) / 10.0) : 1.0 - (dl + zt);
-    ap = al / a.beta64;
+    ap = al / (be > 0.0 ? be : a.beta64);
+  }
+}
+
+// Gap continuation of read position g for a plan with a per-base track: eps_i and
+// beta_i = 1 - eps_i (FP32 from the prepared values, FP64 from the raw Phred value).
+template <typename T>
+__device__ __forceinline__ void row_gap(const FwdArgs &a, int64_t g, T &ep, T &be) {
+  if constexpr (sizeof(T) == 4) {
+    const float2 v = a.rgap[g];
+    ep = v.x;
+    be = v.y;
+  } else {
+    ep = exp10(-qual_at(a.gq, a.qual_f32, g) / 10.0);
+    be = 1.0 - ep;
   }
 }
 
@@ -187,12 +203,13 @@ struct WfState {
 // TOP: lane 0 takes the row above its strip from (tM, tI, tT), already in its own scale,
 // instead of the DP's row 0 (row tiles of long reads: the previous tile's last row).
 // OWN: every lane passes the haplotype code of its own column in `cu` (no code exchange).
+// GQ: a per-base gap-continuation track: row r's D chain takes er[r] instead of eps.
 template <typename T, int L, int K, bool EXT, bool PRIMED = false, bool ABS_E = false,
-          bool TOP = false, bool OWN = false>
+          bool TOP = false, bool OWN = false, bool GQ = false>
 __device__ __forceinline__ void wf_step(WfState<T, K> &st, int cu, int t, T bnd, T eps,
                                         const T *tbl, const T (&ap)[K], const T (&dl)[K],
                                         const T (&zt)[K], const T (&ei)[K], T (&in3)[3],
-                                        T tM = 0, T tI = 0, T tT = 0) {
+                                        T tM = 0, T tI = 0, T tT = 0, const T *er = nullptr) {
   constexpr unsigned FULL = 0xffffffffu;
   constexpr int CS = TableGeom<T, K>::CS;
   if constexpr (OWN) {
@@ -231,12 +248,13 @@ __device__ __forceinline__ void wf_step(WfState<T, K> &st, int cu, int t, T bnd,
   for (int r = K - 1; r >= 0; --r) {
     const T md = r ? st.M[r - 1] : st.Md;
     T sd;
+    const T epr = GQ ? er[r] : eps;
     if constexpr (PRIMED) {
       sd = r ? st.I[r - 1] + zt[r - 1] * st.D[r - 1] : st.Sd;
-      st.D[r] = st.M[r] + eps * st.D[r];            // Eq. 3 over zeta
+      st.D[r] = st.M[r] + epr * st.D[r];            // Eq. 3 over zeta
     } else {
       sd = r ? st.I[r - 1] + st.D[r - 1] : st.Sd;
-      st.D[r] = zt[r] * st.M[r] + eps * st.D[r];    // Eq. 3 (same row, previous column)
+      st.D[r] = zt[r] * st.M[r] + epr * st.D[r];    // Eq. 3 (same row, previous column)
     }
     const T er = ABS_E ? fabs(e[r]) : e[r];
     st.M[r] = er * (ap[r] * md + sd);               // Eq. 1 (previous row, previous column)
@@ -326,12 +344,13 @@ __host__ __device__ constexpr int x2_row(int pos) {
 // One wavefront step of the packed path (extended-range FP32, D/zeta form; the same
 // arithmetic as wf_step<float, L, K, true, true> per lane operation): 3.5 instructions per
 // cell instead of 6; only the I chain down the rows (Eq. 2) stays scalar.
-template <int L, int K, bool TOP = false>
+template <int L, int K, bool TOP = false, bool GQ = false>
 __device__ __forceinline__ void wf_step_x2(WfState2<K> &st, int cu, int t, float bnd, float eps,
                                            const float *tbl, const float2 (&ap)[K / 2],
                                            const float2 (&dl)[K / 2], const float2 (&zt)[K / 2],
                                            const float2 (&ei)[K / 2], float tM = 0.f,
-                                           float tI = 0.f, float tT = 0.f) {
+                                           float tI = 0.f, float tT = 0.f,
+                                           const float2 *er2 = nullptr) {
   constexpr unsigned FULL = 0xffffffffu;
   constexpr int H = K / 2;
   constexpr int CS = TableGeom<float, K>::CS;
@@ -368,7 +387,7 @@ __device__ __forceinline__ void wf_step_x2(WfState2<K> &st, int cu, int t, float
   for (int p = H - 1; p >= 0; --p) {
     const float2 md = p ? st.M[p - 1] : make_float2(st.Md, Mtop);
     const float2 sd = p ? S[p - 1] : make_float2(st.Sd, Stop);
-    st.D[p] = ffma2(eps2, st.D[p], st.M[p]);                               // Eq. 3 over zeta
+    st.D[p] = ffma2(GQ ? er2[p] : eps2, st.D[p], st.M[p]);                 // Eq. 3 over zeta
     st.M[p] = fmul2(make_float2(e[2 * p], e[2 * p + 1]), ffma2(ap[p], md, sd));  // Eq. 1
   }
   // Eq. 2 down the rows: the products with the new M of the row above in pairs, the chain
@@ -434,7 +453,8 @@ constexpr int wf_min_blocks() {
   return sizeof(T) == 8 ? 1 : (K <= 8 ? 4 : (K <= 16 ? 3 : 2));
 }
 
-template <typename T, int L, int K, bool EXT>
+// GQ: the batch has a per-base gap-continuation track (row r takes eps_r and beta_r).
+template <typename T, int L, int K, bool EXT, bool GQ = false>
 __global__ void __launch_bounds__(128, wf_min_blocks<T, K>()) wf_forward(const FwdArgs a) {
   using G_ = TableGeom<T, K>;
   constexpr int G = 32 / L;
@@ -490,6 +510,15 @@ __global__ void __launch_bounds__(128, wf_min_blocks<T, K>()) wf_forward(const F
       } else {
         bad = true;
       }
+#ifdef PHMM_DEBUG
+      // the pair's read positions and haplotype codes (with their guards) inside the buffers
+      if (!bad && a.dbg_err &&
+          (r0 + m > a.dbg_sum_m || hs < kHapGuard ||
+           hs + ((n + 15) & ~(int64_t)15) + kHapGuard > a.dbg_hcode_bytes)) {
+        atomicOr(a.dbg_err, kDbgPairIndex);
+        bad = true;
+      }
+#endif
       if (bad) {
         m = 0;
         n = 0;
@@ -524,6 +553,7 @@ __global__ void __launch_bounds__(128, wf_min_blocks<T, K>()) wf_forward(const F
     // (folded exactly into the row's emission, delta and I coefficients), which offsets the
     // typical decay of the forward values down the rows so one exponent covers the lane.
     T ap[K], dl[K], zt[K], ei[K], M[K], I[K], D[K];
+    T er[GQ ? K : 1];  // per-row gap continuation (track only)
 #pragma unroll
     for (int r0v = 0; r0v < K; r0v += VW) {
       T ev[kCodes][VW];
@@ -540,14 +570,19 @@ __global__ void __launch_bounds__(128, wf_min_blocks<T, K>()) wf_forward(const F
         const T bias = rr ? (T)(1 << kBias) : (T)1;
         M[rr] = 0;
         D[rr] = 0;
+        T epr = eps, ber = beta;
+        if constexpr (GQ) {
+          if (pos >= 0) row_gap<T>(a, r0 + pos, epr, ber);
+          er[rr] = epr;
+        }
         if (pos >= 0) {
           T Q;
-          row_params<T>(a, r0 + pos, ap[rr], dl[rr], zt[rr], Q);
+          row_params<T>(a, r0 + pos, ap[rr], dl[rr], zt[rr], Q, GQ ? (double)ber : 0.0);
           const int code = a.rcode[r0 + pos];
-          ei[rr] = pos == 0 ? (T)0 : eps * bias;
+          ei[rr] = pos == 0 ? (T)0 : epr * bias;
           dl[rr] *= bias;
           I[rr] = 0;
-          const T em = bias * (beta * ((T)1 - Q)), ex = bias * (beta * (Q / (T)3));
+          const T em = bias * (ber * ((T)1 - Q)), ex = bias * (ber * (Q / (T)3));
 #pragma unroll
           for (int c = 0; c < kNull; ++c)
             ev[c][u] = (c == code || c == kN || code == kN) ? em : ex;
@@ -577,9 +612,11 @@ __global__ void __launch_bounds__(128, wf_min_blocks<T, K>()) wf_forward(const F
     st.f = t == 0 ? (T)1 : Num<T>::exp2i(-kBias * (K - 1));
     st.E = 0;
     float2 ap2[X2 ? H : 1], dl2[X2 ? H : 1], zt2[X2 ? H : 1], ei2[X2 ? H : 1];
+    float2 er2[X2 && GQ ? H : 1];
     if constexpr (X2) {
 #pragma unroll
       for (int q = 0; q < H; ++q) {
+        if constexpr (GQ) er2[q] = make_float2(er[q], er[q + H]);
         st.M[q] = make_float2(M[q], M[q + H]);
         st.I[q] = make_float2(I[q], I[q + H]);
         st.D[q] = make_float2(D[q], D[q + H]);
@@ -635,10 +672,11 @@ __global__ void __launch_bounds__(128, wf_min_blocks<T, K>()) wf_forward(const F
           tT = bX * cv;
         }
         if constexpr (X2) {
-          wf_step_x2<L, K, true>(st, code, t, bnd, eps, tbl, ap2, dl2, zt2, ei2, tM, tI, tT);
+          wf_step_x2<L, K, true, GQ>(st, code, t, bnd, eps, tbl, ap2, dl2, zt2, ei2, tM, tI, tT,
+                                     er2);
         } else {
-          wf_step<T, L, K, EXT, EXT, false, true>(st, code, t, bnd, eps, tbl, ap, dl, zt, ei,
-                                                  in3, tM, tI, tT);
+          wf_step<T, L, K, EXT, EXT, false, true, false, GQ>(st, code, t, bnd, eps, tbl, ap, dl,
+                                                             zt, ei, in3, tM, tI, tT, er);
         }
         if (!last_tile && t == L - 1) {
           const int64_t j = (int64_t)s + 1 - (L - 1);  // the last lane's column
@@ -658,9 +696,11 @@ __global__ void __launch_bounds__(128, wf_min_blocks<T, K>()) wf_forward(const F
           }
         }
       } else if constexpr (X2) {
-        wf_step_x2<L, K>(st, code, t, bnd, eps, tbl, ap2, dl2, zt2, ei2);
+        wf_step_x2<L, K, false, GQ>(st, code, t, bnd, eps, tbl, ap2, dl2, zt2, ei2, 0.f, 0.f, 0.f,
+                                    er2);
       } else {
-        wf_step<T, L, K, EXT, EXT>(st, code, t, bnd, eps, tbl, ap, dl, zt, ei, in3);
+        wf_step<T, L, K, EXT, EXT, false, false, false, GQ>(st, code, t, bnd, eps, tbl, ap, dl, zt,
+                                                            ei, in3, 0, 0, 0, er);
       }
     };
     auto load_cols = [&](int s0) {

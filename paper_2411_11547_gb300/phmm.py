@@ -13,13 +13,16 @@ import threading
 import numpy as np
 
 PHMM_OK, PHMM_EINVAL, PHMM_ETOOLONG, PHMM_ENOMEM, PHMM_ECUDA, PHMM_ESTATE = 0, -1, -2, -3, -4, -5
+PHMM_EGUARD = -6  # debug builds: a guard region or a kernel index check failed
 PHMM_MAX_READ_LEN = 512
 FLAG_FP32, FLAG_RESCUED64, FLAG_EXTENDED, FLAG_INVALID = 1, 2, 4, 8
 QUAL_U8, QUAL_F32 = 0, 1
 FIRST_PLAIN32, FIRST_EXT32 = 0, 1
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_PKG, "libphmm.so")
+# PHMM_DEBUG=1: the debug build (guard regions and kernel index checks, see _build.py)
+_LIB_PATH = os.path.join(_PKG, "libphmm_debug.so" if os.environ.get("PHMM_DEBUG") == "1"
+                         else "libphmm.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -42,6 +45,7 @@ class Batch(ctypes.Structure):
         ("read_off", ctypes.c_void_p), ("hap_bases", ctypes.c_void_p),
         ("hap_off", ctypes.c_void_p), ("pair_read", ctypes.c_void_p),
         ("pair_hap", ctypes.c_void_p), ("gcp", ctypes.c_double),
+        ("gcp_q", ctypes.c_void_p),
     ]
 
 
@@ -64,7 +68,8 @@ def lib():
     with _lock:
         if _lib is None:
             if not os.path.exists(_LIB_PATH):
-                raise ImportError(f"libphmm.so not built at {_LIB_PATH}; run the package build")
+                raise ImportError(f"{os.path.basename(_LIB_PATH)} not built at {_LIB_PATH}; run "
+                                  f"the package build")
             L = ctypes.CDLL(_LIB_PATH)
             vp, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)
             L.phmm_options_default.argtypes = [ctypes.POINTER(Options)]
@@ -78,11 +83,12 @@ def lib():
             L.phmm_plan_info.restype = ctypes.c_int
             L.phmm_forward.argtypes = [vp, vp, ctypes.c_size_t, vp, vp, vp]
             L.phmm_forward.restype = ctypes.c_int
-            L.phmm_backward.argtypes = [vp, vp, ctypes.c_size_t, vp, vp, vp, vp, vp, vp]
+            L.phmm_backward.argtypes = [vp, vp, ctypes.c_size_t, vp, vp, vp, vp, vp, vp, vp]
             L.phmm_backward.restype = ctypes.c_int
             L.phmm_forward_partials.argtypes = [vp, vp, ctypes.c_size_t, vp, vp, vp]
             L.phmm_forward_partials.restype = ctypes.c_int
-            L.phmm_backward_partials.argtypes = [vp, vp, ctypes.c_size_t, vp, vp, vp, vp, vp, vp]
+            L.phmm_backward_partials.argtypes = [vp, vp, ctypes.c_size_t, vp, vp, vp, vp, vp, vp,
+                                                 vp]
             L.phmm_backward_partials.restype = ctypes.c_int
             L.phmm_plan_destroy.argtypes = [vp]
             L.phmm_plan_destroy.restype = None
@@ -107,7 +113,7 @@ def lib():
                                           ctypes.c_int64, vp, vp]
             L.phmm_score_host.restype = ctypes.c_int
             L.phmm_grad_host.argtypes = [ctypes.POINTER(Batch), ctypes.POINTER(Options),
-                                         ctypes.c_int64, vp, vp, vp, vp, vp, vp, vp]
+                                         ctypes.c_int64, vp, vp, vp, vp, vp, vp, vp, vp]
             L.phmm_grad_host.restype = ctypes.c_int
             L.phmm_score_host_release.argtypes = []
             L.phmm_score_host_release.restype = None
@@ -170,12 +176,15 @@ class DeviceBatch:
         self.pair_hap = dev(batch["pair_hap"], torch.int32)
         self.gcp = float(batch["gcp"])
         self.alpha_mode = int(batch.get("alpha_mode", 0))
+        gq = batch.get("gcp_q")
+        self.gcp_q = dev(gq, qt) if gq is not None else None
 
     @classmethod
     def from_tensors(cls, read_bases, base_q, ins_q, del_q, read_off, hap_bases, hap_off,
-                     pair_read, pair_hap, gcp, alpha_mode=0):
+                     pair_read, pair_hap, gcp, alpha_mode=0, gcp_q=None):
         """Wrap tensors already on the device (no copy).  The quals are uint8 or float32; the
-        offsets int64, the pair lists int32, all contiguous."""
+        offsets int64, the pair lists int32, all contiguous.  gcp_q: an optional per-base
+        gap-continuation track (the quals' dtype, one value per read base)."""
         import torch
         self = cls.__new__(cls)
         self.host = None
@@ -198,6 +207,11 @@ class DeviceBatch:
             setattr(self, k, t)
         self.gcp = float(gcp)
         self.alpha_mode = int(alpha_mode)
+        if gcp_q is not None and (gcp_q.dtype != base_q.dtype or not gcp_q.is_contiguous()
+                                  or gcp_q.device != read_bases.device
+                                  or gcp_q.numel() != base_q.numel()):
+            raise TypeError("gcp_q: need a contiguous tensor like base_q")
+        self.gcp_q = gcp_q
         return self
 
     @property
@@ -221,6 +235,7 @@ class DeviceBatch:
         b.pair_read = self.pair_read.data_ptr() if b.n_pairs else None
         b.pair_hap = self.pair_hap.data_ptr() if b.n_pairs else None
         b.gcp = self.gcp
+        b.gcp_q = self.gcp_q.data_ptr() if self.gcp_q is not None else None
         return b
 
 
@@ -262,9 +277,12 @@ class Plan:
             raise PhmmError(rc, "phmm_forward")
         return out, flags
 
-    def backward(self, dL, stream=None):
-        """phmm_backward: d(loss)/d(quals) given dL = d(loss)/d(log10 L) (after forward)."""
-        return self._grad(lib().phmm_backward, "phmm_backward", dL, stream)
+    def backward(self, dL, stream=None, out=None):
+        """phmm_backward: d(loss)/d(quals) given dL = d(loss)/d(log10 L) (after forward):
+        (d_base_q, d_ins_q, d_del_q, d_gcp), plus d_gcp_q for a batch with a per-base
+        gap-continuation track.  `out`: optional tensors of that tuple to write into (the
+        per-base ones of at least sum_m elements)."""
+        return self._grad(lib().phmm_backward, "phmm_backward", dL, stream, out)
 
     def forward_partials(self, out=None, flags=None, stream=None):
         """phmm_forward_partials: log10 L and flags from the adjoint sweep's own forward pass,
@@ -285,27 +303,39 @@ class Plan:
             raise PhmmError(rc, "phmm_forward_partials")
         return out, flags
 
-    def backward_partials(self, dL, stream=None):
+    def backward_partials(self, dL, stream=None, out=None):
         """phmm_backward_partials: the partials of the latest forward_partials weighted by dL
-        and reduced per read (same outputs as backward)."""
-        return self._grad(lib().phmm_backward_partials, "phmm_backward_partials", dL, stream)
+        and reduced per read (same outputs and `out` as backward).  Calls that repeat the
+        previous call's pointers (pass `out` and the same dL tensor) replay a captured CUDA
+        graph on small batches."""
+        return self._grad(lib().phmm_backward_partials, "phmm_backward_partials", dL, stream,
+                          out)
 
-    def _grad(self, fn, name, dL, stream):
+    def _grad(self, fn, name, dL, stream, out=None):
         import torch
         dev = self.dbatch.read_bases.device
         tot = max(self.sum_m, 1)
-        dbq = torch.empty(tot, dtype=torch.float32, device=dev)
-        diq = torch.empty(tot, dtype=torch.float32, device=dev)
-        ddq = torch.empty(tot, dtype=torch.float32, device=dev)
-        dgcp = torch.empty(1, dtype=torch.float64, device=dev)
-        dL = dL.to(device=dev, dtype=torch.float64).contiguous()
+        track = self.dbatch.gcp_q is not None
+        if out is not None:
+            dbq, diq, ddq, dgcp = out[:4]
+            dgq = out[4] if track else None
+        else:
+            dbq = torch.empty(tot, dtype=torch.float32, device=dev)
+            diq = torch.empty(tot, dtype=torch.float32, device=dev)
+            ddq = torch.empty(tot, dtype=torch.float32, device=dev)
+            dgq = torch.empty(tot, dtype=torch.float32, device=dev) if track else None
+            dgcp = torch.empty(1, dtype=torch.float64, device=dev)
+        if dL.device != dev or dL.dtype != torch.float64 or not dL.is_contiguous():
+            dL = dL.to(device=dev, dtype=torch.float64).contiguous()
         rc = fn(self.handle, ctypes.c_void_p(self._ws_ptr), self.ws_bytes,
                 ctypes.c_void_p(dL.data_ptr()), ctypes.c_void_p(dbq.data_ptr()),
                 ctypes.c_void_p(diq.data_ptr()), ctypes.c_void_p(ddq.data_ptr()),
+                ctypes.c_void_p(dgq.data_ptr() if track else 0),
                 ctypes.c_void_p(dgcp.data_ptr()), _stream(stream))
         if rc != PHMM_OK:
             raise PhmmError(rc, name)
-        return dbq[: self.sum_m], diq[: self.sum_m], ddq[: self.sum_m], dgcp
+        out = (dbq[: self.sum_m], diq[: self.sum_m], ddq[: self.sum_m], dgcp)
+        return out + (dgq[: self.sum_m],) if track else out
 
     def launch_count(self, which=0):
         return int(lib().phmm_plan_launch_count(self.handle, which))
@@ -387,6 +417,7 @@ def host_batch_struct(batch, keep):
     b.pair_read = arr("pair_read", np.int32)
     b.pair_hap = arr("pair_hap", np.int32)
     b.gcp = float(batch["gcp"])
+    b.gcp_q = arr("gcp_q", qdt) if batch.get("gcp_q") is not None else None
     return b
 
 
@@ -409,7 +440,8 @@ def grad_host(batch, dL, opts: Options | None = None, subset_cells: int = 1 << 3
     """phmm_grad_host: log10 L, flags and d(loss)/d(base_q, ins_q, del_q, gcp) (numpy) of a
     batch held in host memory, given dL = d(loss)/d(log10 L) per pair (host), in pipelined
     subsets of about `subset_cells` cells.  `out`: optional preallocated
-    (log10 [P] f64, flags [P] u8, dbq, diq, ddq [sum m] f32) arrays to write into."""
+    (log10 [P] f64, flags [P] u8, dbq, diq, ddq [sum m] f32) arrays to write into.  A batch
+    with a per-base gap-continuation track ("gcp_q") also returns d_gcp_q [sum m]."""
     keep = []
     b = host_batch_struct(batch, keep)
     P = b.n_pairs
@@ -422,13 +454,16 @@ def grad_host(batch, dL, opts: Options | None = None, subset_cells: int = 1 << 3
     dL = np.ascontiguousarray(dL, dtype=np.float64)
     if dL.shape != (P,):
         raise ValueError("dL must hold one value per pair")
+    track = batch.get("gcp_q") is not None
+    gq = np.empty(sm, dtype=np.float32) if track else None
     gg = ctypes.c_double()
     rc = lib().phmm_grad_host(ctypes.byref(b), ctypes.byref(opts) if opts is not None else None,
                               int(subset_cells), dL.ctypes.data, y.ctypes.data, flags.ctypes.data,
-                              gb.ctypes.data, gi.ctypes.data, gd.ctypes.data, ctypes.byref(gg))
+                              gb.ctypes.data, gi.ctypes.data, gd.ctypes.data,
+                              gq.ctypes.data if track else None, ctypes.byref(gg))
     if rc != PHMM_OK:
         raise PhmmError(rc, "phmm_grad_host")
-    return y, flags, gb, gi, gd, gg.value
+    return (y, flags, gb, gi, gd, gg.value) + ((gq,) if track else ())
 
 
 def probe_pipe(kind: int, iters: int = 4000):

@@ -69,10 +69,11 @@ def test_plan_create_rejects_bad_arguments_on_host(lib):
 def test_forward_rejects_null_plan(lib):
     from paper_2411_11547_gb300 import phmm
     assert lib.phmm_forward(None, None, 0, None, None, None) == phmm.PHMM_EINVAL
-    assert lib.phmm_backward(None, None, 0, None, None, None, None, None, None) == phmm.PHMM_EINVAL
+    assert lib.phmm_backward(None, None, 0, None, None, None, None, None, None,
+                             None) == phmm.PHMM_EINVAL
     assert lib.phmm_forward_partials(None, None, 0, None, None, None) == phmm.PHMM_EINVAL
     assert lib.phmm_backward_partials(None, None, 0, None, None, None, None, None,
-                                      None) == phmm.PHMM_EINVAL
+                                      None, None) == phmm.PHMM_EINVAL
     assert lib.phmm_workspace_bytes(None) == 0
 
 
@@ -140,11 +141,16 @@ def test_grad_host_rejects_bad_input_before_touching_the_gpu(lib):
     g = [np.empty(sm, dtype=np.float32) for _ in range(3)]
     gg = ctypes.c_double()
     dL = np.ones(6)
-    args = [out.ctypes.data, fl.ctypes.data] + [x.ctypes.data for x in g] + [ctypes.byref(gg)]
+    args = ([out.ctypes.data, fl.ctypes.data] + [x.ctypes.data for x in g] + [None]
+            + [ctypes.byref(gg)])
     assert lib.phmm_grad_host(ctypes.byref(s), None, 10, None, *args) == phmm.PHMM_EINVAL
-    no_grad = args[:2] + [None, None, None, ctypes.byref(gg)]
+    no_grad = args[:2] + [None, None, None, None, ctypes.byref(gg)]
     assert lib.phmm_grad_host(ctypes.byref(s), None, 10, dL.ctypes.data,
                               *no_grad) == phmm.PHMM_EINVAL
+    # a batch with a per-base gap-continuation track needs the d_gcp_q array
+    tr = phmm.host_batch_struct(dict(b, gcp_q=np.full(sm, 10, np.uint8)), keep)
+    assert lib.phmm_grad_host(ctypes.byref(tr), None, 10, dL.ctypes.data,
+                              *args) == phmm.PHMM_EINVAL
     bad = dict(b, pair_hap=b["pair_hap"].copy())
     bad["pair_hap"][2] = 99
     s2 = phmm.host_batch_struct(bad, keep)

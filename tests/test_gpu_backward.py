@@ -309,3 +309,38 @@ def test_every_pair_in_fp64(phmm, fused):
     grad_close(gi, wi, "d/diq", ro)
     grad_close(gd, wd, "d/ddq", ro)
     assert abs(gg - wg) <= 1e-6 * abs(wg) + 1e-9, (gg, wg)
+
+
+def test_fused_step_graph_replay(phmm):
+    """On a small batch the fused step's two calls replay captured CUDA graphs: results equal
+    the eager launches bit for bit, replays repeat them, new output pointers recapture, and
+    the launch count is reported either way."""
+    import torch
+    b = synth.c3_grad(pairs=16 * 64)  # one C0-shaped region, 1,024 pairs
+    P = len(b["pair_read"])
+    dy = torch.as_tensor(np.random.default_rng(4).uniform(-1, 1, P), device="cuda")
+    res = {}
+    for g in (0, 1):
+        plan = phmm.Plan(phmm.DeviceBatch(b), phmm.options(use_graph=g))
+        y = torch.empty(P, dtype=torch.float64, device="cuda")
+        fl = torch.empty(P, dtype=torch.uint8, device="cuda")
+        sm = int(b["read_off"][-1])
+        gout = tuple(torch.empty(sm, dtype=torch.float32, device="cuda") for _ in range(3)) + (
+            torch.empty(1, dtype=torch.float64, device="cuda"),)
+        outs = []
+        for _ in range(3):  # the 2nd call repeats the pointers (capture), the 3rd replays
+            plan.forward_partials(y, fl)
+            gr = plan.backward_partials(dy, out=gout)
+            torch.cuda.synchronize()
+            outs.append([y.cpu().numpy(), fl.cpu().numpy()] + [x.cpu().numpy() for x in gr])
+            assert plan.launch_count(0) > 10 and plan.launch_count(1) > 3
+        assert plan.backward_ms()[0] == (-1.0 if g else plan.backward_ms()[0])
+        for o in outs[1:]:
+            for u, v in zip(outs[0], o):
+                assert np.array_equal(u, v)
+        res[g] = outs[0]
+    for u, v in zip(res[0], res[1]):
+        assert np.array_equal(u, v)
+    wy, wb, wi, wd, wg = oracle.backward_batch(b, dy.cpu().numpy())
+    assert np.all(np.abs(res[1][0] - wy) <= 1e-3)
+    grad_close(res[1][2], wb, "d/dbq graph", b["read_off"])

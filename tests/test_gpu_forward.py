@@ -289,7 +289,6 @@ def test_long_reads_in_row_tiles(phmm, first_line):
     # reads longer than one group (512 rows) are swept in row tiles of 512, alone and mixed
     # with short reads in one binned batch; the plain first line sends them through the
     # tiled FP64 and per-lane-exponent FP64 kernels
-    import torch
     rng = np.random.default_rng(31)
     regs = []
     for m, n in [(513, 700), (600, 40), (1024, 1100), (1500, 300), (2048, 2100), (777, 777),
@@ -315,10 +314,14 @@ def test_long_reads_in_row_tiles(phmm, first_line):
     b["pair_hap"] = np.concatenate([b["pair_hap"], short["pair_hap"] + nh]).astype(np.int32)
     got, flags, plan = run(phmm, b, first_line=first_line)
     check(got, flags, oracle.forward_batch(b), phmm)
-    # the adjoint has no row tiles
-    with pytest.raises(phmm.PhmmError) as e:
-        plan.backward(torch.ones(len(got), dtype=torch.float64, device="cuda"))
-    assert e.value.status == phmm.PHMM_ETOOLONG
+    # the adjoint sweeps the same row tiles (bottom to top): gradients against the oracle's,
+    # through phmm_backward and through the fused step, in FP32 and with every pair in FP64
+    from test_gpu_backward import check_against_oracle
+    dy = np.random.default_rng(first_line).uniform(-1, 1, len(got))
+    bf = dict(b, base_q=b["base_q"].astype(np.float32), ins_q=b["ins_q"].astype(np.float32),
+              del_q=b["del_q"].astype(np.float32))
+    check_against_oracle(phmm, bf, dy, first_line=first_line,
+                         adjoint_rescue=2 if first_line == 0 else 1)
 
 
 def test_metamorphic_order_blocks_and_bins(phmm):
