@@ -47,9 +47,9 @@ BWD_OPS_SCOPE = 25
 # subsets on the 3e11-cell step (measured best of 2^33..2^37 on GB300)
 E2E_SUBSET_CELLS = 1 << 37
 # DRAM bytes per cell of the adjoint kernel (read + written: its checkpoints), from an ncu
-# capture of wf_backward<float,16,10> on the 4.5e9-cell c3_grad batch (10.35 GB read, 13.73 GB
+# capture of wf_backward<float,16,10> on the 4.5e9-cell c3_grad batch (10.19 GB read, 13.73 GB
 # written); the c4 step's traffic is this times its cells.
-BWD_DRAM_BYTES_PER_CELL = (10.350 + 13.733) * 1e9 / 4.5e9
+BWD_DRAM_BYTES_PER_CELL = (10.194 + 13.735) * 1e9 / 4.5e9
 
 WORKLOAD_DESC = {
     "c4_persistent": "65,536 regions x 4 haplotypes x 16 reads = 2^22 pairs; read length "
@@ -417,14 +417,10 @@ def main():
         d2h = out_h.numel() * 8 + g_h.numel() * 4 + 8
 
         def e2e_step():
-            db = phmm.DeviceBatch.__new__(phmm.DeviceBatch)
-            db.host = batch
-            db.qual_dtype = dbatch.qual_dtype
-            for k in ("read_bases", "base_q", "ins_q", "del_q", "read_off", "hap_bases",
-                      "hap_off", "pair_read", "pair_hap"):
-                setattr(db, k, hb[k].to(dev, non_blocking=True))
-            db.gcp = float(batch["gcp"])
-            db.alpha_mode = 0
+            td = {k: hb[k].to(dev, non_blocking=True)
+                  for k in ("read_bases", "base_q", "ins_q", "del_q", "read_off", "hap_bases",
+                            "hap_off", "pair_read", "pair_hap")}
+            db = phmm.DeviceBatch.from_tensors(gcp=float(batch["gcp"]), alpha_mode=0, **td)
             pl = phmm.Plan(db, opts)
             o, _ = pl.forward_partials()
             gb, gi, gd, gg = pl.backward_partials(dL)
