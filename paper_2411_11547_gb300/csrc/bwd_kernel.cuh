@@ -49,6 +49,10 @@ __host__ __device__ constexpr int rec_width(int K) { return rec_w(K, (int)sizeof
 // Shared memory of one warp: the emission table (kCodes planes of 32 lanes x LS, as
 // TableGeom) and the step records of one segment.  The segment length follows from what fits
 // next to the table at the occupancy the registers allow (warps per SM): 2 to 8 steps.
+// kBwdRecLast: the segment's last step is recorded too, so the reverse reads every step's
+// forward values from shared memory and the forward state is dead while it runs (fewer
+// registers live across the reverse, at one step less per segment).
+constexpr bool kBwdRecLast = true;
 __host__ __device__ constexpr int bwd_warps_per_sm(int K, int elem) {
   return elem == 8 ? 4 : (K <= 4 ? 16 : (K <= 6 ? 12 : 8));
 }
@@ -61,17 +65,22 @@ __host__ __device__ constexpr size_t bwd_table_bytes(int K, int elem) {
 __host__ __device__ constexpr size_t bwd_rec_bytes(int K, int elem) {
   return (size_t)32 * rec_w(K, elem) * elem;
 }
-// Step records that fit next to the table (the last step of a segment needs none: its state
-// is still in registers), so a segment is one step longer.
+// Step records that fit next to the table (without kBwdRecLast the last step of a segment
+// needs none: its state is still in registers, so a segment is one step longer).
 __host__ __device__ constexpr int bwd_rec_fit(int K, int elem) {
   return (int)(((size_t)227 * 1024 / bwd_warps_per_sm(K, elem) - 256 - bwd_table_bytes(K, elem)) /
                bwd_rec_bytes(K, elem));
 }
 __host__ __device__ constexpr int bwd_seg_len(int K, int elem) {
-  return bwd_rec_fit(K, elem) + 1 > 8 ? 8 : (bwd_rec_fit(K, elem) + 1 < 2 ? 2 : bwd_rec_fit(K, elem) + 1);
+  return bwd_rec_fit(K, elem) + (kBwdRecLast ? 0 : 1) > 8
+             ? 8
+             : (bwd_rec_fit(K, elem) + (kBwdRecLast ? 0 : 1) < 2
+                    ? 2
+                    : bwd_rec_fit(K, elem) + (kBwdRecLast ? 0 : 1));
 }
 __host__ __device__ constexpr size_t bwd_warp_bytes(int K, int elem) {
-  return bwd_table_bytes(K, elem) + (size_t)(bwd_seg_len(K, elem) - 1) * bwd_rec_bytes(K, elem);
+  return bwd_table_bytes(K, elem) +
+         (size_t)(bwd_seg_len(K, elem) - (kBwdRecLast ? 0 : 1)) * bwd_rec_bytes(K, elem);
 }
 
 // Records are stored as [record][16-byte group][lane], so one warp-wide 128-bit access
@@ -589,22 +598,30 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
       adj_rescale<T, L, K, kBias>(as, t, Sseed, ES);
       // Partial sums, each held as (true value) x 2^-H, the lane's accumulator scale.
       // Per row r: gA (alpha_r: u(r,j+1) M(r-1,j)), gD (delta_r: I^(r,j) M(r-1,j)),
-      // gZ (zeta_r: D^(r,j+1) M(r,j)), gY (M^(r,j) M(r,j)), gX (its mismatch-column part
+      // gZ (zeta_r: D^(r,j+1) M(r,j)), gX (the mismatch-column part of M^(r,j) M(r,j),
       // times -e_mismatch).  gAl / gDl: the products for the lower lane's row 0.
-      // Lane scalars: gS (beta: u S of the row above), gEI (eps via I), gED (eps via D).
-      // With a per-base track the lane scalars are kept per row instead: gSr (beta_r),
+      // Lane scalars: gEI (eps via I: I^(r+1,j) I(r,j) over the lane's rows, the lower
+      // lane's row 0 apart in gEIe), gED (eps via D), gMe (M at row m: seed x M(m,j)).
+      // The M occupancy per row (sum_j M^ M) and the beta sum are not accumulated: flow
+      // conservation of the posterior gives them from the sums above (phase C).
+      // With a per-base track the beta and eps sums are kept per row instead: gSr (beta_r),
       // gEIr and gEDr (eps_r), with gSl / gEIl the lower lane's row 0.
-      T gA[K], gD[K], gZ[K], gY[K], gX[K];
+      T gA[K], gD[K], gZ[K], gX[K];
 #pragma unroll
-      for (int r = 0; r < K; ++r) gA[r] = gD[r] = gZ[r] = gY[r] = gX[r] = 0;
-      T gAl = 0, gDl = 0, gS = 0, gEI = 0, gED = 0;
+      for (int r = 0; r < K; ++r) gA[r] = gD[r] = gZ[r] = gX[r] = 0;
+      T gAl = 0, gDl = 0, gEI = 0, gEIe = 0, gED = 0, gMe = 0;
       T gSr[GQ ? K : 1], gEIr[GQ ? K : 1], gEDr[GQ ? K : 1], gSl = 0, gEIl = 0;
 #pragma unroll
       for (int r = 0; r < (GQ ? K : 1); ++r) gSr[r] = gEIr[r] = gEDr[r] = 0;
       int H = kNoScale;
       // lane 0's row above its strip (row 0 of the DP, or a pad row): S = K0 D(0, j); below
       // the first tile that row is the tile above's last row, whose lane forms the product
-      const T bndS = (t == 0 && tile == 0) ? bnd : (T)0;
+      // (per-base track only: the scalar beta sum follows from flow conservation)
+      const T bndS = (GQ && t == 0 && tile == 0) ? bnd : (T)0;
+      // a lane holding pad rows: its forward I there (the row-0 boundary passed down) is
+      // taken as zero in the reverse, so products across pad rows vanish without a per-row
+      // test (the per-base track's beta_r sums keep the boundary)
+      const bool padl = !GQ && first > 0;
       // the last lane of a tile above another: the tile below's first-row adjoints of the
       // segment's columns (lane u: the column of reverse step b + u), and the exponent and
       // size of the next ones to arrive (for the lane's renormalisation)
@@ -666,7 +683,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
         // recompute the segment, recording the lane's rows after each step (column b+u2+1-t)
         for (int u2 = 0; u2 < len; ++u2) {
           fstep(code_at(codes, u2), u2, cb, above != nullptr);
-          if (u2 < len - 1) {  // the last step's state stays in registers
+          if (kBwdRecLast || u2 < len - 1) {  // else the last step's state stays in registers
             T rec[RW];
 #pragma unroll
             for (int r = 0; r < K; ++r) {
@@ -680,7 +697,8 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
           }
         }
         const int EF = st.E;
-        const T fS = bndS * Num<T>::exp2i(-EF);  // lane 0's boundary row in its own scale
+        // lane 0's boundary row in its own scale (per-base track only)
+        const T fS = GQ ? bndS * Num<T>::exp2i(-EF) : (T)0;
         if (__any_sync(FULL, pend))
           adj_rescale<T, L, K, kBias>(as, t, Sseed, ES, pend, H != kNoScale, H - EF,
                                       ain != nullptr, Eo, xo);
@@ -690,13 +708,23 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
           const int64_t j = (int64_t)b + u2 + 1 - t;  // this lane's column at this step
           const int c = code_at(codes, u2);
           // forward values of the lane's rows at column j: M, I, D/zeta (rec[r], [K+r], [2K+r])
+          // (the other rows' I follow from the top row's by Eq. 2; a lane holding pad rows
+          // takes its top I as zero, which makes I zero down to its first real row, where
+          // I is zero anyway)
           T rec[3 * K];
-          if (u2 == len - 1) {
+          bool rebuild = true;
+          if (!kBwdRecLast && u2 == len - 1) {
 #pragma unroll
             for (int r = 0; r < K; ++r) {
               rec[r] = st.M[r];
-              rec[K + r] = st.I[r];
               rec[2 * K + r] = st.D[r];
+            }
+            if constexpr (GQ) {
+#pragma unroll
+              for (int r = 0; r < K; ++r) rec[K + r] = st.I[r];
+              rebuild = false;
+            } else {
+              rec[K] = st.I[0];
             }
           } else {
             T sr[RW];
@@ -707,6 +735,9 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
               rec[2 * K + r] = sr[K + r];
             }
             rec[K] = sr[2 * K];
+          }
+          if constexpr (!GQ) rec[K] = padl ? (T)0 : rec[K];
+          if (rebuild) {
 #pragma unroll
             for (int r = 1; r < K; ++r) rec[K + r] = dl[r] * rec[r - 1] + ei[r] * rec[K + r - 1];
           }
@@ -769,14 +800,14 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
                 gA[r] *= sc;
                 gD[r] *= sc;
                 gZ[r] *= sc;
-                gY[r] *= sc;
                 gX[r] *= sc;
               }
               gAl *= sc;
               gDl *= sc;
-              gS *= sc;
               gEI *= sc;
+              gEIe *= sc;
               gED *= sc;
+              gMe *= sc;
               if constexpr (GQ) {
 #pragma unroll
                 for (int r = 0; r < K; ++r) {
@@ -817,21 +848,23 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
               const T Mb = r == K - 1 ? Mb0 + sd : Mb0;
               // I^(r, j): one FMA on the row-to-row chain; eps x I^(r+1, j) again for the
               // partial
+              // I^(r, j): one FMA on the row-to-row chain
               const T Ib = fma(eiB, Ibl, r == K - 1 ? uba + sd : uba);
-              const T Il = eiB * Ibl;
               const T Dn = uba + (GQ ? er[r] : eps) * as.Db[r];            // D^(r, j)
               const T un = e[r] * Mb;                                      // u(r, j)
               {
                 if (r == K - 1) {
                   gAl += uba * Mv;
                   gDl += Ibl * Mv;
+                  gMe += sd * Mv;
                 } else {
                   gA[r + 1] += uba * Mv;
                   gD[r + 1] += Ibl * Mv;
                 }
-                // the I -> I partial counts only where the row below is a real row (pad rows
-                // pass the boundary down with a nonzero coefficient)
                 if constexpr (GQ) {
+                  // the I -> I partial counts only where the row below is a real row (pad
+                  // rows pass the boundary down with a nonzero coefficient)
+                  const T Il = eiB * Ibl;
                   if (r == K - 1) {
                     gSl += uba * (Iv + zt[r] * Dv);
                     gEIl += (r + 1 > first ? Il : (T)0) * Iv;
@@ -841,12 +874,14 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
                   }
                   gEDr[r] += zD * Dv;
                 } else {
-                  gS += uba * (Iv + zt[r] * Dv);
-                  gEI += (r + 1 > first ? Il : (T)0) * Iv;
+                  // eps x I^(r+1, j) I(r, j) with the row's coefficient eps x bias applied
+                  // in phase C; the pad rows' I is zero here (padl), and the coefficient of
+                  // a first real row is zero, so only real-to-real transitions count
+                  if (r == K - 1) gEIe += Ibl * Iv;
+                  else gEI += Ibl * Iv;
                   gED += zD * Dv;
                 }
                 gZ[r] += as.Db[r] * Mv;
-                gY[r] += Mb * Mv;
                 gX[r] += fmin(un, (T)0) * Mv;
               }
               ub = as.u[r];
@@ -856,7 +891,6 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
             }
             // lane 0's row above: u(0, j+1) times the boundary S = K0 D(0, j)
             if constexpr (GQ) gSr[0] += fabs(ub) * fS;
-            else gS += fabs(ub) * fS;
           }
           as.Itop = Ibl;
           if constexpr (TILED) {
@@ -887,6 +921,17 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
       // accumulators to true values; the products of a row's I^ with the row above's M
       // carry one row bias less than the others (x 2^kBias), except across the lane edge
       const T sc = H == kNoScale ? (T)0 : Num<T>::exp2i(H);
+      // M occupancy of each row, sum_j M^(r,j) M(r,j): by flow conservation at M(r,j) it
+      // is the sum over the cell's out-transitions (to M(r+1,j+1), I(r+1,j), D(r,j+1)) and,
+      // at row m, the path's end, each weighted by its coefficient as the reverse step
+      // forms M^ (the same scale and row biases)
+      T gY[K];
+#pragma unroll
+      for (int r = 0; r < K; ++r) {
+        const T y = r == K - 1 ? fma(apb, gAl, fma(dlb, gDl, gMe))
+                               : fma(ap[r + 1], gA[r + 1], dl[r + 1] * gD[r + 1]);
+        gY[r] = fma(zt[r], gZ[r], y) * sc;
+      }
       gAl *= sc;
       gDl *= sc;
       T dAlpha[K], dDelta[K];
@@ -895,7 +940,6 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
         dAlpha[r] = gA[r] * sc;
         dDelta[r] = gD[r] * (sc * (T)(1 << kBias));
         gZ[r] *= sc;
-        gY[r] *= sc;
         gX[r] *= sc;
       }
       {
@@ -904,10 +948,32 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
         dAlpha[0] = t == 0 ? (T)0 : aup;
         dDelta[0] = t == 0 ? (T)0 : dup;
       }
-      // pad lanes' scalar sums are garbage by construction
-      T gSs = real_lane ? gS * sc : (T)0, gEs = real_lane ? (gED + gEI / eps) * sc : (T)0;
-      T spec = 0;  // the beta term of M(1,1), true value (see below)
-      if (t == 0 && tile == 0 && first <= K) {
+      // eps: the I -> I products carry one row bias less (x 2^kBias) except across the
+      // lane edge.  beta (scalar gap continuation): flow conservation at the M states gives
+      // the expected number of transitions into M through beta (from I, from D, and the
+      // start from D(0, .)) as that of the transitions out of M into I and D plus the
+      // path's end in M at row m: sum over the rows of delta_r dDelta_r + zeta_r dZeta_r,
+      // plus seed x sum_j M(m,j).  Pad lanes' scalar sums are zero or discarded.
+      T gSs = 0, gEs = real_lane ? (gED + (T)(1 << kBias) * gEI + gEIe) * sc : (T)0;
+      if constexpr (!GQ) {
+        gSs = gMe * sc;
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+          const int pos = tile * LK + t * K + r - npad;
+          if (pos >= 0) {
+            T dum, del, zet, Q;
+            row_params<T>(fa, r0 + pos, dum, del, zet, Q);
+            gSs = fma(del, dDelta[r], fma(zet, gZ[r], gSs));
+          }
+        }
+        if (TILED && !last_tile && t == L - 1) {
+          // the next tile's first row: its M -> I transitions pair this lane's last row
+          const T del = dlb;  // that row's delta (unbiased)
+          gSs = fma(del, gDl, gSs);
+        }
+      }
+      T spec = 0;  // the beta term of M(1,1), true value (per-base track; see below)
+      if (GQ && t == 0 && tile == 0 && first <= K) {
         // Lane 0 never visits column 0, so when lane 0 holds row 1 or the row above it, the
         // beta term of M(1,1) = lambda beta D(0,0), u(1,1) S(0,0), is added here: the reverse
         // sweep ended at column 1 (as.u holds u(., 1); as.diagU the lower lane's u(row 0, 1)),
