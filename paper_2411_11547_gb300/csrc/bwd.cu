@@ -96,15 +96,15 @@ int bwd_cfg_supported(int cfg) {
   return cfg >= 0 && cfg < kNumCfg32 && bwd_kernel32(cfg_lanes(cfg), cfg_rows(cfg)) != nullptr;
 }
 
-static size_t bwd_smem(int K, int elem, int block) {
-  return (size_t)(block / 32) * bwd_warp_bytes(K, elem);
+static size_t bwd_smem(int K, int elem, int block, bool gq) {
+  return (size_t)(block / 32) * bwd_warp_bytes(K, elem, gq);
 }
 
-// Threads per block of an adjoint launch: warps_per_block warps, fewer where their shared
-// memory would exceed the per-block limit.
-static int bwd_block(int K, int elem, int warps_per_block) {
-  const int fit = (int)((size_t)227 * 1024 / bwd_warp_bytes(K, elem));
-  return 32 * std::max(1, std::min(warps_per_block, fit));
+// Threads per block of an adjoint launch: warps_per_block warps, fewer where the group's
+// launch bounds allow fewer or their shared memory would exceed the per-block limit.
+static int bwd_block(int K, int elem, int warps_per_block, bool gq) {
+  const int fit = (int)((size_t)227 * 1024 / bwd_warp_bytes(K, elem, gq));
+  return 32 * std::max(1, std::min({warps_per_block, bwd_max_wpb(K, elem, gq), fit}));
 }
 
 // Read length -> FP32 backward group (rows per lane <= 12 keeps the adjoint in registers).
@@ -127,8 +127,8 @@ static int blocks_per_sm(BwdKernel k, size_t smem, int block) {
 }
 
 // Checkpoints per pair group: one per ramp step, then one per segment.
-static int64_t bwd_nchk(int L, int K, int elem, int64_t n_max) {
-  const int seg = bwd_seg_len(K, elem);
+static int64_t bwd_nchk(int L, int K, int elem, int64_t n_max, bool gq) {
+  const int seg = bwd_seg_len(K, elem, gq);
   const int64_t steps = n_max + L - 1 + seg;
   const int64_t ramp = (L + 15) & ~15;
   return ramp + (steps + seg - 1) / seg + 2;
@@ -144,8 +144,8 @@ static int ntile_cap(int L, int K, int max_m) {
 // A slot (elements of the kernel's type): the checkpoints of every row tile, then for tiled
 // plans the last row of every tile but the last and two buffers of a tile's first-row
 // adjoints, each n_max columns of 4 values.
-static int64_t slot_elems(int L, int K, int elem, int64_t n_max, int ntile) {
-  int64_t e = (int64_t)ntile * bwd_nchk(L, K, elem, n_max) * 32 * ck_w(K, elem);
+static int64_t slot_elems(int L, int K, int elem, int64_t n_max, int ntile, bool gq) {
+  int64_t e = (int64_t)ntile * bwd_nchk(L, K, elem, n_max, gq) * 32 * ck_w(K, elem);
   if (ntile > 1) e += (int64_t)(ntile - 1 + 2) * n_max * 4;
   return e;
 }
@@ -181,25 +181,26 @@ static BwdLayout bwd_layout(const phmm_plan *pl) {
   Lo.red = take(reduce_scratch_bytes_aligned(b.n_pairs, b.n_reads));
   size_t slots = 0;
   const int64_t nmax = plan_n_max(pl);
+  const bool gq = plan_gq(pl);
   for (int cfg : plan_bwd_used(pl)) {
     const int L = cfg_lanes(cfg), K = cfg_rows(cfg);
-    const int block = bwd_block(K, 4, wpb);
+    const int block = bwd_block(K, 4, wpb, gq);
     const size_t nslot = (size_t)plan_sms(pl) *
-                         blocks_per_sm(bwd_kernel32(L, K, plan_gq(pl)), bwd_smem(K, 4, block),
+                         blocks_per_sm(bwd_kernel32(L, K, gq), bwd_smem(K, 4, block, gq),
                                        block) *
                          (block / 32);
     slots = std::max(slots, nslot * 4 * (size_t)slot_elems(L, K, 4, nmax,
-                                                             ntile_cap(L, K, plan_max_m(pl))));
+                                                             ntile_cap(L, K, plan_max_m(pl)), gq));
   }
   for (int c = 0; c < kNumCfg64; ++c) {
     const int K = rows64(c);
-    const int block = bwd_block(K, 8, wpb);
+    const int block = bwd_block(K, 8, wpb, gq);
     const size_t nslot = (size_t)plan_sms(pl) *
-                         blocks_per_sm(bwd_kernel64(K, plan_gq(pl)), bwd_smem(K, 8, block),
+                         blocks_per_sm(bwd_kernel64(K, gq), bwd_smem(K, 8, block, gq),
                                        block) *
                          (block / 32);
     slots = std::max(slots, nslot * 8 * (size_t)slot_elems(32, K, 8, nmax,
-                                                             ntile_cap(32, K, plan_max_m(pl))));
+                                                             ntile_cap(32, K, plan_max_m(pl)), gq));
   }
   Lo.slots = take(slots);
   Lo.slots_bytes = slots;
@@ -304,17 +305,17 @@ int bwd_sweep_impl(phmm_plan *pl, char *ws, const double *dL, double *out, uint8
       c.f.offset_dev = grp_begin + cfg;
       c.f.count_dev = grp_count + cfg;
       c.f.counter = (int32_t *)(ws + plan_layout_bin(pl, 7)) + cfg;
-      c.nchk = (int32_t)bwd_nchk(L, K, 4, nmax);
+      c.nchk = (int32_t)bwd_nchk(L, K, 4, nmax, plan_gq(pl));
       c.ntile_cap = ntile_cap(L, K, plan_max_m(pl));
       c.ck_tile = (int64_t)c.nchk * 32 * ck_w(K, 4);
       c.tile_cols = nmax;
-      c.slot_elems = slot_elems(L, K, 4, nmax, c.ntile_cap);
+      c.slot_elems = slot_elems(L, K, 4, nmax, c.ntile_cap, plan_gq(pl));
       c.rescue = o.adjoint_rescue ? 0 : 1;  // without the FP64 pass, failures write NaN
       c.all64 = o.adjoint_rescue == 2 ? 1 : 0;
       BwdKernel k = bwd_kernel32(L, K, plan_gq(pl));
       if (!k) return (int)cudaErrorInvalidValue;
-      const int block = bwd_block(K, 4, o.bwd_warps_per_block);
-      const size_t sm = bwd_smem(K, 4, block);
+      const int block = bwd_block(K, 4, o.bwd_warps_per_block, plan_gq(pl));
+      const size_t sm = bwd_smem(K, 4, block, plan_gq(pl));
       const int grid = plan_sms(pl) * blocks_per_sm(k, sm, block);
       c.f.dbg_nslots = (int64_t)(Lo.slots_bytes / (4 * (size_t)c.slot_elems));
       k<<<grid, block, sm, s>>>(c);
@@ -329,15 +330,15 @@ int bwd_sweep_impl(phmm_plan *pl, char *ws, const double *dL, double *out, uint8
       c.f.offset_dev = nullptr;
       c.f.count_dev = rcnt + k64;
       c.f.counter = rctr + k64;
-      c.nchk = (int32_t)bwd_nchk(32, K, 8, nmax);
+      c.nchk = (int32_t)bwd_nchk(32, K, 8, nmax, plan_gq(pl));
       c.ntile_cap = ntile_cap(32, K, plan_max_m(pl));
       c.ck_tile = (int64_t)c.nchk * 32 * ck_w(K, 8);
       c.tile_cols = nmax;
-      c.slot_elems = slot_elems(32, K, 8, nmax, c.ntile_cap);
+      c.slot_elems = slot_elems(32, K, 8, nmax, c.ntile_cap, plan_gq(pl));
       c.rescue = 1;
       BwdKernel kk = bwd_kernel64(K, plan_gq(pl));
-      const int block = bwd_block(K, 8, o.bwd_warps_per_block);
-      const size_t sm = bwd_smem(K, 8, block);
+      const int block = bwd_block(K, 8, o.bwd_warps_per_block, plan_gq(pl));
+      const size_t sm = bwd_smem(K, 8, block, plan_gq(pl));
       const int grid = plan_sms(pl) * blocks_per_sm(kk, sm, block);
       c.f.dbg_nslots = (int64_t)(Lo.slots_bytes / (8 * (size_t)c.slot_elems));
       kk<<<grid, block, sm, s>>>(c);

@@ -53,8 +53,19 @@ __host__ __device__ constexpr int rec_width(int K) { return rec_w(K, (int)sizeof
 // forward values from shared memory and the forward state is dead while it runs (fewer
 // registers live across the reverse, at one step less per segment).
 constexpr bool kBwdRecLast = true;
-__host__ __device__ constexpr int bwd_warps_per_sm(int K, int elem) {
-  return elem == 8 ? 4 : (K <= 4 ? 16 : (K <= 6 ? 12 : 8));
+// gq: the kernels of batches with a per-base gap-continuation track (more registers per row;
+// they share the scalar kernels' geometry).  More warps per SM for the 8- and 10-row groups
+// (10 and 9, at shorter segments) measured 1-5% slower on the 2^22-pair batch.
+__host__ __device__ constexpr int bwd_warps_per_sm(int K, int elem, bool gq = false) {
+  return (void)gq, elem == 8 ? 4 : (K <= 4 ? 16 : (K <= 6 ? 12 : 8));
+}
+// Most warps per block of a group's launch: the largest divisor (up to 4) of its warps per SM,
+// so that whole blocks fill the SM.
+__host__ __device__ constexpr int bwd_max_wpb(int K, int elem, bool gq = false) {
+  return bwd_warps_per_sm(K, elem, gq) % 4 == 0
+             ? 4
+             : (bwd_warps_per_sm(K, elem, gq) % 3 == 0 ? 3
+                                                       : (bwd_warps_per_sm(K, elem, gq) % 2 == 0 ? 2 : 1));
 }
 __host__ __device__ constexpr size_t bwd_table_bytes(int K, int elem) {
   return (size_t)kCodes * 32 * elem *
@@ -67,20 +78,20 @@ __host__ __device__ constexpr size_t bwd_rec_bytes(int K, int elem) {
 }
 // Step records that fit next to the table (without kBwdRecLast the last step of a segment
 // needs none: its state is still in registers, so a segment is one step longer).
-__host__ __device__ constexpr int bwd_rec_fit(int K, int elem) {
-  return (int)(((size_t)227 * 1024 / bwd_warps_per_sm(K, elem) - 256 - bwd_table_bytes(K, elem)) /
+__host__ __device__ constexpr int bwd_rec_fit(int K, int elem, bool gq = false) {
+  return (int)(((size_t)227 * 1024 / bwd_warps_per_sm(K, elem, gq) - 256 - bwd_table_bytes(K, elem)) /
                bwd_rec_bytes(K, elem));
 }
-__host__ __device__ constexpr int bwd_seg_len(int K, int elem) {
-  return bwd_rec_fit(K, elem) + (kBwdRecLast ? 0 : 1) > 8
+__host__ __device__ constexpr int bwd_seg_len(int K, int elem, bool gq = false) {
+  return bwd_rec_fit(K, elem, gq) + (kBwdRecLast ? 0 : 1) > 8
              ? 8
-             : (bwd_rec_fit(K, elem) + (kBwdRecLast ? 0 : 1) < 2
+             : (bwd_rec_fit(K, elem, gq) + (kBwdRecLast ? 0 : 1) < 2
                     ? 2
-                    : bwd_rec_fit(K, elem) + (kBwdRecLast ? 0 : 1));
+                    : bwd_rec_fit(K, elem, gq) + (kBwdRecLast ? 0 : 1));
 }
-__host__ __device__ constexpr size_t bwd_warp_bytes(int K, int elem) {
+__host__ __device__ constexpr size_t bwd_warp_bytes(int K, int elem, bool gq = false) {
   return bwd_table_bytes(K, elem) +
-         (size_t)(bwd_seg_len(K, elem) - (kBwdRecLast ? 0 : 1)) * bwd_rec_bytes(K, elem);
+         (size_t)(bwd_seg_len(K, elem, gq) - (kBwdRecLast ? 0 : 1)) * bwd_rec_bytes(K, elem);
 }
 
 // Records are stored as [record][16-byte group][lane], so one warp-wide 128-bit access
@@ -201,22 +212,23 @@ __device__ __forceinline__ void adj_rescale(AdjState<T, K> &as, int t, T S, int 
   as.seed = (t == L - 1 && S > (T)0) ? Num<T>::exp2i(-ES - as.EB) / S : (T)0;
 }
 
-// Minimum resident blocks per SM the compiler must allow: the per-row registers (forward
-// state, adjoints, coefficients, five partial sums) grow with the rows per lane.
-template <typename T, int K>
-constexpr int bwd_min_blocks() {
-  return sizeof(T) == 8 ? 1 : (K <= 4 ? 4 : (K <= 6 ? 3 : 2));
+// Register cap per thread for the group's warps per SM (the per-row registers: forward
+// state, adjoints, coefficients, four partial sums, grow with the rows per lane).
+__host__ __device__ constexpr int bwd_max_regs(int K, int elem, bool gq) {
+  return 65536 / (32 * bwd_warps_per_sm(K, elem, gq)) / 8 * 8 > 255
+             ? 255
+             : 65536 / (32 * bwd_warps_per_sm(K, elem, gq)) / 8 * 8;
 }
 
 // GQ: the batch has a per-base gap-continuation track: row r takes eps_r and beta_r, and the
 // gap-continuation partials are kept per row (three more sums per row) for d/dgcp_r.
 template <typename T, int L, int K, bool GQ = false>
-__global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const BwdArgs a) {
+__global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const BwdArgs a) {
   using G_ = TableGeom<T, K>;
   constexpr int G = 32 / L, VW = G_::VW, LS = G_::LS, CS = G_::CS;
   constexpr int kBias = 2;
   constexpr int CKW = ck_width<T>(K), RW = rec_width<T>(K);
-  constexpr int kSeg = bwd_seg_len(K, sizeof(T));
+  constexpr int kSeg = bwd_seg_len(K, sizeof(T), GQ);
   // Range of the posterior scale exponent h = E_fwd + E_adj over which the raw products of
   // stored forward and adjoint values are accumulated: below kHmin a product is at most
   // 2^(16 + kHmin) of a posterior (dropped); above kHmax the products a lane needs can fall
@@ -240,7 +252,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks<T, K>()) wf_backward(const
   // per warp: the table of signed emissions beta * lambda (+ for a match, - for a mismatch)
   // and the segment's step records
   static_assert(bwd_table_bytes(K, sizeof(T)) == (size_t)kCodes * CS * sizeof(T), "table");
-  unsigned char *wsm = smem_raw + (size_t)warp * bwd_warp_bytes(K, sizeof(T));
+  unsigned char *wsm = smem_raw + (size_t)warp * bwd_warp_bytes(K, sizeof(T), GQ);
   T *tblE = reinterpret_cast<T *>(wsm) + lane * LS;
   T *recS = reinterpret_cast<T *>(wsm + bwd_table_bytes(K, sizeof(T)));
   const int wpb = blockDim.x >> 5;
