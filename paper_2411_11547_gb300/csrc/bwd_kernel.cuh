@@ -143,6 +143,25 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// A lane's share of a record ([16-byte group][lane] layout, W elements) copied from global to
+// shared memory asynchronously (16 bytes per copy, bypassing L1); cp_async_wait waits for
+// every copy the thread has issued.
+template <typename T, int W>
+__device__ __forceinline__ void rec_copy_async(T *dst, const T *src, int lane) {
+  constexpr int V = 16 / (int)sizeof(T);
+#pragma unroll
+  for (int g = 0; g < W / V; ++g) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + (size_t)(g * 32 + lane) * V);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d),
+                 "l"(src + (size_t)(g * 32 + lane) * V)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // Small integers (exponents, base codes) ride in the records as exact floating values.
 template <typename T>
 __device__ __forceinline__ T int_bits(int e) {
@@ -651,6 +670,14 @@ __global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const Bw
       // reverse, when that segment's forward exponent EF is known: a lane then keeps
       // EF + EB = H where it can, so its partial sums need no re-basing.
       bool pend = false;
+      // The checkpoint of the segment to the left is copied (cp.async) into the last two
+      // step-record slots once the reverse has read them, so the next restore reads shared
+      // memory.  Every record access is lane-private ([group][lane] layout, each lane its own
+      // 16-byte groups), so no warp synchronisation is needed.
+      static_assert(CKW <= 2 * RW, "a checkpoint fits in two record slots");
+      constexpr bool kPf = kBwdRecLast && kSeg >= 3;
+      T *const ckS = recS + (size_t)(kSeg - 2) * 32 * RW;
+      bool ck_smem = false;
       for (int q = nq - 1; q >= 0; --q) {
         const int b = q < ramp ? q : ramp + kSeg * (q - ramp);
         const int len = q < ramp ? 1 : kSeg;
@@ -659,7 +686,13 @@ __global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const Bw
         bool nzq;
         {
           T ck[CKW];
-          rec_load<T, CKW, true>(ckt + (size_t)q * 32 * CKW, lane, ck);
+          if (ck_smem) {  // copied into the record slots during the previous segment's reverse
+            cp_async_wait();
+            rec_load<T, CKW>(ckS, lane, ck);
+          } else {
+            rec_load<T, CKW, true>(ckt + (size_t)q * 32 * CKW, lane, ck);
+          }
+          ck_smem = false;
 #pragma unroll
           for (int r = 0; r < K; ++r) {
             st.M[r] = ck[r];
@@ -717,6 +750,11 @@ __global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const Bw
         pend = false;
         // reverse over the segment
         for (int u2 = len - 1; u2 >= 0; --u2) {
+          // slots kSeg-2 and kSeg-1 are free from here on (a one-step segment uses slot 0)
+          if (kPf && q > 0 && u2 == (len == 1 ? 0 : len - 3)) {
+            rec_copy_async<T, CKW>(ckS, ckt + (size_t)(q - 1) * 32 * CKW, lane);
+            ck_smem = true;
+          }
           const int64_t j = (int64_t)b + u2 + 1 - t;  // this lane's column at this step
           const int c = code_at(codes, u2);
           // forward values of the lane's rows at column j: M, I, D/zeta (rec[r], [K+r], [2K+r])
