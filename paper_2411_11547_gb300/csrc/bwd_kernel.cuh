@@ -31,12 +31,14 @@ struct BwdArgs {
   int32_t *why;                   // [2]: hand-offs for the scale range / non-finite partials
 };
 
-// Widths (elements, multiples of the 16-byte vector) of a checkpoint (K rows of M, I, D/zeta
-// plus the boundary values, the conversion factor and the exponent) and of a step record (K
-// rows of M and D/zeta plus the top row's I: the other rows' I follow from Eq. 2 again).
+// Widths (elements, multiples of the 16-byte vector) of a checkpoint (K rows of M and D/zeta,
+// the top row's I, the boundary values, the conversion factor and the exponent) and of a step
+// record (K rows of M and D/zeta plus the top row's I).  Both leave the other rows' I out:
+// Eq. 2 gives them again from M and the top row's I.  Both start with the same values in the
+// same order, so the lane's registers feed either store alike.
 __host__ __device__ constexpr int vecw(int elem) { return 16 / elem; }
 __host__ __device__ constexpr int ck_w(int K, int elem) {
-  return (3 * K + 4 + vecw(elem) - 1) / vecw(elem) * vecw(elem);
+  return (2 * K + 5 + vecw(elem) - 1) / vecw(elem) * vecw(elem);
 }
 __host__ __device__ constexpr int rec_w(int K, int elem) {
   return (2 * K + 1 + vecw(elem) - 1) / vecw(elem) * vecw(elem);
@@ -524,15 +526,15 @@ __global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const Bw
 #pragma unroll
           for (int r = 0; r < K; ++r) {
             ck[r] = st.M[r];
-            ck[K + r] = st.I[r];
-            ck[2 * K + r] = st.D[r];
+            ck[K + r] = st.D[r];
           }
-          ck[3 * K] = st.Md;
-          ck[3 * K + 1] = st.Sd;
-          ck[3 * K + 2] = st.f;
-          ck[3 * K + 3] = int_bits<T>(2 * st.E + (nzA ? 1 : 0));
+          ck[2 * K] = st.I[0];
+          ck[2 * K + 1] = st.Md;
+          ck[2 * K + 2] = st.Sd;
+          ck[2 * K + 3] = st.f;
+          ck[2 * K + 4] = int_bits<T>(2 * st.E + (nzA ? 1 : 0));
 #pragma unroll
-          for (int k = 3 * K + 4; k < CKW; ++k) ck[k] = 0;
+          for (int k = 2 * K + 5; k < CKW; ++k) ck[k] = 0;
           rec_store<T, CKW, true>(ckt + (size_t)q * 32 * CKW, lane, ck);
         }
         TileCol<T> cb = {0, 0, 0, 0};
@@ -696,13 +698,17 @@ __global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const Bw
 #pragma unroll
           for (int r = 0; r < K; ++r) {
             st.M[r] = ck[r];
-            st.I[r] = ck[K + r];
-            st.D[r] = ck[2 * K + r];
+            st.D[r] = ck[K + r];
           }
-          st.Md = ck[3 * K];
-          st.Sd = ck[3 * K + 1];
-          st.f = ck[3 * K + 2];
-          const int ef = bits_int<T>(ck[3 * K + 3]);
+          st.I[0] = ck[2 * K];
+          // the other rows' I by Eq. 2, as the forward step formed them (power-of-two
+          // renormalisation commutes with it)
+#pragma unroll
+          for (int r = 1; r < K; ++r) st.I[r] = dl[r] * st.M[r - 1] + ei[r] * st.I[r - 1];
+          st.Md = ck[2 * K + 1];
+          st.Sd = ck[2 * K + 2];
+          st.f = ck[2 * K + 3];
+          const int ef = bits_int<T>(ck[2 * K + 4]);
           st.E = ef >> 1;
           nzq = (ef & 1) != 0;
         }
@@ -749,13 +755,15 @@ __global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const Bw
                                       ain != nullptr, Eo, xo);
         pend = false;
         // reverse over the segment
+        // slots kSeg-2 and kSeg-1 are free from reverse step pf_u on (a one-step segment
+        // uses slot 0 only)
+        const int pf_u = (kPf && q > 0) ? (len == 1 ? 0 : len - 3) : -1;
         for (int u2 = len - 1; u2 >= 0; --u2) {
-          // slots kSeg-2 and kSeg-1 are free from here on (a one-step segment uses slot 0)
-          if (kPf && q > 0 && u2 == (len == 1 ? 0 : len - 3)) {
+          if (u2 == pf_u) {
             rec_copy_async<T, CKW>(ckS, ckt + (size_t)(q - 1) * 32 * CKW, lane);
             ck_smem = true;
           }
-          const int64_t j = (int64_t)b + u2 + 1 - t;  // this lane's column at this step
+          const int j = b + u2 + 1 - t;  // this lane's column at this step (n < 2^30)
           const int c = code_at(codes, u2);
           // forward values of the lane's rows at column j: M, I, D/zeta (rec[r], [K+r], [2K+r])
           // (the other rows' I follow from the top row's by Eq. 2; a lane holding pad rows
@@ -815,18 +823,14 @@ __global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const Bw
               rU *= as.fB;
               rI *= as.fB;
             }
-          } else {
-            if (t == L - 1) {
-              rU = 0;
-              rI = 0;
-            } else {
-              rU *= as.fB;
-              rI *= as.fB;
-            }
+          } else {  // fB is zero in the last lane (no lane below)
+            rU *= as.fB;
+            rI *= as.fB;
           }
           const T ubK = as.diagU;
           as.diagU = rU;
-          const T sd = (t == L - 1 && j >= 1 && j <= n) ? as.seed : (T)0;
+          // the seed is nonzero in the last lane of the last tile only
+          const T sd = (uint32_t)(j - 1) < (uint32_t)n ? as.seed : (T)0;
           // Posterior scale 2^(EF + EB): products of stored forward and adjoint values are
           // accumulated raw, the accumulators re-based when the scale changes.  Lanes whose
           // forward or adjoint values are all zero contribute nothing; h > kHmax with both
