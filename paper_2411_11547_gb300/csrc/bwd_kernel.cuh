@@ -33,28 +33,25 @@ struct BwdArgs {
 
 // Widths (elements, multiples of the 16-byte vector) of a checkpoint (K rows of M and D/zeta,
 // the top row's I, the boundary values, the conversion factor and the exponent) and of a step
-// record (K rows of M and D/zeta plus the top row's I).  Both leave the other rows' I out:
-// Eq. 2 gives them again from M and the top row's I.  Both start with the same values in the
-// same order, so the lane's registers feed either store alike.
+// record (K rows of M and D/zeta; the step's top-row I goes to a side array of one element
+// per lane).  Both leave the other rows' I out: Eq. 2 gives them again from M and the top
+// row's I.  Both start with the same values in the same order, so the lane's registers feed
+// either store alike.
 __host__ __device__ constexpr int vecw(int elem) { return 16 / elem; }
 __host__ __device__ constexpr int ck_w(int K, int elem) {
   return (2 * K + 5 + vecw(elem) - 1) / vecw(elem) * vecw(elem);
 }
-__host__ __device__ constexpr int rec_w(int K, int elem) {
-  return (2 * K + 1 + vecw(elem) - 1) / vecw(elem) * vecw(elem);
-}
+__host__ __device__ constexpr int rec_w(int K, int elem) { return (void)elem, 2 * K; }
 template <typename T>
 __host__ __device__ constexpr int ck_width(int K) { return ck_w(K, (int)sizeof(T)); }
 template <typename T>
 __host__ __device__ constexpr int rec_width(int K) { return rec_w(K, (int)sizeof(T)); }
 
 // Shared memory of one warp: the emission table (kCodes planes of 32 lanes x LS, as
-// TableGeom) and the step records of one segment.  The segment length follows from what fits
-// next to the table at the occupancy the registers allow (warps per SM): 2 to 8 steps.
-// kBwdRecLast: the segment's last step is recorded too, so the reverse reads every step's
-// forward values from shared memory and the forward state is dead while it runs (fewer
-// registers live across the reverse, at one step less per segment).
-constexpr bool kBwdRecLast = true;
+// TableGeom) and the step records of one segment (every step, the last one included, so the
+// reverse reads every step's forward values from shared memory and the forward state is dead
+// while it runs), then the steps' top-row I.  The segment length follows from what fits next
+// to the table at the occupancy the registers allow (warps per SM): 2 to 8 steps.
 // gq: the kernels of batches with a per-base gap-continuation track (more registers per row;
 // they share the scalar kernels' geometry).  More warps per SM for the 8- and 10-row groups
 // (10 and 9, at shorter segments) measured 1-5% slower on the 2^22-pair batch.
@@ -75,25 +72,20 @@ __host__ __device__ constexpr size_t bwd_table_bytes(int K, int elem) {
               ? (K + vecw(elem) - 1) / vecw(elem) * vecw(elem)
               : (K + vecw(elem) - 1) / vecw(elem) * vecw(elem) + vecw(elem));
 }
+// Shared memory of one step: its record and its top-row I.
 __host__ __device__ constexpr size_t bwd_rec_bytes(int K, int elem) {
-  return (size_t)32 * rec_w(K, elem) * elem;
+  return (size_t)32 * (rec_w(K, elem) + 1) * elem;
 }
-// Step records that fit next to the table (without kBwdRecLast the last step of a segment
-// needs none: its state is still in registers, so a segment is one step longer).
+// Steps whose records fit next to the table.
 __host__ __device__ constexpr int bwd_rec_fit(int K, int elem, bool gq = false) {
   return (int)(((size_t)227 * 1024 / bwd_warps_per_sm(K, elem, gq) - 256 - bwd_table_bytes(K, elem)) /
                bwd_rec_bytes(K, elem));
 }
 __host__ __device__ constexpr int bwd_seg_len(int K, int elem, bool gq = false) {
-  return bwd_rec_fit(K, elem, gq) + (kBwdRecLast ? 0 : 1) > 8
-             ? 8
-             : (bwd_rec_fit(K, elem, gq) + (kBwdRecLast ? 0 : 1) < 2
-                    ? 2
-                    : bwd_rec_fit(K, elem, gq) + (kBwdRecLast ? 0 : 1));
+  return bwd_rec_fit(K, elem, gq) > 8 ? 8 : (bwd_rec_fit(K, elem, gq) < 2 ? 2 : bwd_rec_fit(K, elem, gq));
 }
 __host__ __device__ constexpr size_t bwd_warp_bytes(int K, int elem, bool gq = false) {
-  return bwd_table_bytes(K, elem) +
-         (size_t)(bwd_seg_len(K, elem, gq) - (kBwdRecLast ? 0 : 1)) * bwd_rec_bytes(K, elem);
+  return bwd_table_bytes(K, elem) + (size_t)bwd_seg_len(K, elem, gq) * bwd_rec_bytes(K, elem);
 }
 
 // Records are stored as [record][16-byte group][lane], so one warp-wide 128-bit access
@@ -276,6 +268,8 @@ __global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const Bw
   unsigned char *wsm = smem_raw + (size_t)warp * bwd_warp_bytes(K, sizeof(T), GQ);
   T *tblE = reinterpret_cast<T *>(wsm) + lane * LS;
   T *recS = reinterpret_cast<T *>(wsm + bwd_table_bytes(K, sizeof(T)));
+  T *recI = recS + (size_t)kSeg * 32 * RW;  // [step][lane]: the step's top-row I
+  static_assert(RW % vecw(sizeof(T)) == 0, "records of whole 16-byte groups");
   const int wpb = blockDim.x >> 5;
   T *slot = reinterpret_cast<T *>(a.scratch) + (size_t)(blockIdx.x * wpb + warp) * a.slot_elems;
   T *ckb = slot;
@@ -677,7 +671,7 @@ __global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const Bw
       // memory.  Every record access is lane-private ([group][lane] layout, each lane its own
       // 16-byte groups), so no warp synchronisation is needed.
       static_assert(CKW <= 2 * RW, "a checkpoint fits in two record slots");
-      constexpr bool kPf = kBwdRecLast && kSeg >= 3;
+      constexpr bool kPf = kSeg >= 3;
       T *const ckS = recS + (size_t)(kSeg - 2) * 32 * RW;
       bool ck_smem = false;
       for (int q = nq - 1; q >= 0; --q) {
@@ -734,17 +728,15 @@ __global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const Bw
         // recompute the segment, recording the lane's rows after each step (column b+u2+1-t)
         for (int u2 = 0; u2 < len; ++u2) {
           fstep(code_at(codes, u2), u2, cb, above != nullptr);
-          if (kBwdRecLast || u2 < len - 1) {  // else the last step's state stays in registers
+          {
             T rec[RW];
 #pragma unroll
             for (int r = 0; r < K; ++r) {
               rec[r] = st.M[r];
               rec[K + r] = st.D[r];
             }
-            rec[2 * K] = st.I[0];
-#pragma unroll
-            for (int k = 2 * K + 1; k < RW; ++k) rec[k] = 0;
             rec_store<T, RW>(recS + (size_t)u2 * 32 * RW, lane, rec);
+            recI[u2 * 32 + lane] = st.I[0];
           }
         }
         const int EF = st.E;
@@ -770,21 +762,7 @@ __global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const Bw
           // takes its top I as zero, which makes I zero down to its first real row, where
           // I is zero anyway)
           T rec[3 * K];
-          bool rebuild = true;
-          if (!kBwdRecLast && u2 == len - 1) {
-#pragma unroll
-            for (int r = 0; r < K; ++r) {
-              rec[r] = st.M[r];
-              rec[2 * K + r] = st.D[r];
-            }
-            if constexpr (GQ) {
-#pragma unroll
-              for (int r = 0; r < K; ++r) rec[K + r] = st.I[r];
-              rebuild = false;
-            } else {
-              rec[K] = st.I[0];
-            }
-          } else {
+          {
             T sr[RW];
             rec_load<T, RW>(recS + (size_t)u2 * 32 * RW, lane, sr);
 #pragma unroll
@@ -792,13 +770,11 @@ __global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const Bw
               rec[r] = sr[r];
               rec[2 * K + r] = sr[K + r];
             }
-            rec[K] = sr[2 * K];
+            rec[K] = recI[u2 * 32 + lane];
           }
           if constexpr (!GQ) rec[K] = padl ? (T)0 : rec[K];
-          if (rebuild) {
 #pragma unroll
-            for (int r = 1; r < K; ++r) rec[K + r] = dl[r] * rec[r - 1] + ei[r] * rec[K + r - 1];
-          }
+          for (int r = 1; r < K; ++r) rec[K + r] = dl[r] * rec[r - 1] + ei[r] * rec[K + r - 1];
           T e[K];
           load_rows<T, K>(tblE + c * CS, e);
           T rU = __shfl_down_sync(FULL, as.u[0], 1, L);
