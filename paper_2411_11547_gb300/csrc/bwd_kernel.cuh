@@ -188,8 +188,9 @@ struct AdjState {
 // otherwise it normalises the largest to [1, 2).
 // ovr: the last lane of a row tile above another takes the lane below's exponent and size
 // from (Eo, xo), the tile below's first-row adjoints about to arrive, for its adoption.
+// rS: 1/S with L = S 2^(ES - kBias (K-1)), for the lane that seeds row m (else 0).
 template <typename T, int L, int K, int kBias>
-__device__ __forceinline__ void adj_rescale(AdjState<T, K> &as, int t, T S, int ES,
+__device__ __forceinline__ void adj_rescale(AdjState<T, K> &as, int t, T rS, int ES,
                                             bool apply = true, bool keep = false, int Ek = 0,
                                             bool ovr = false, int Eo = 0, T xo = 0) {
   constexpr unsigned FULL = 0xffffffffu;
@@ -222,7 +223,7 @@ __device__ __forceinline__ void adj_rescale(AdjState<T, K> &as, int t, T S, int 
   if (apply && zero && (t < L - 1 || last_ovr))
     as.EB = Elow - kBias * (K - 1) + (xbl > (T)0 ? Num<T>::ilog2(xbl) : 0);
   as.fB = t < L - 1 ? Num<T>::exp2i(Elow - as.EB - kBias * (K - 1)) : (T)0;
-  as.seed = (t == L - 1 && S > (T)0) ? Num<T>::exp2i(-ES - as.EB) / S : (T)0;
+  as.seed = (t == L - 1 && rS > (T)0) ? Num<T>::exp2i(-ES - as.EB) * rS : (T)0;
 }
 
 // Register cap per thread for the group's warps per SM (the per-row registers: forward
@@ -407,8 +408,15 @@ __global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const Bw
 
     int steps = n > 0 ? (int)n + L - 1 : 0;
     steps = __reduce_max_sync(FULL, steps);
+    // The wavefront enters the lanes one per step over the first roundup16(L) steps (the
+    // ramp): there the lanes renormalise after every step, so an empty lane adopts the
+    // exponent of the values about to reach it (two-step ramp segments measured wrong
+    // gradients); then every kSeg steps.  Segment q < ramp is step q; regular segments start
+    // at step ramp.
     const int ramp = steps < ((L + 15) & ~15) ? steps : ((L + 15) & ~15);
     const int nq = ramp + (steps - ramp + kSeg - 1) / kSeg;
+    auto seg_begin = [&](int qq) { return qq < ramp ? qq : ramp + kSeg * (qq - ramp); };
+    auto seg_len = [&](int qq) { return qq < ramp ? 1 : kSeg; };
     const int fin = n > 0 ? (int)n + L - 1 : 0;
 #ifdef PHMM_DEBUG
     // every checkpoint of the warp's longest pair inside the slot (warp-uniform)
@@ -427,7 +435,7 @@ __global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const Bw
     constexpr uint64_t kNullCodes = 0x0505050505050505ull;
     auto seg_codes = [&](int qq) -> uint64_t {
       if (qq < 0 || qq >= nq || n <= 0) return kNullCodes;
-      const int bb = qq < ramp ? qq : ramp + kSeg * (qq - ramp);
+      const int bb = seg_begin(qq);
       int64_t i0 = (int64_t)bb - t;  // 0-based haplotype position of the window's first step
       if (i0 > n) i0 = n;
       const uintptr_t addr = (uintptr_t)(fa.hcode + hs + i0);
@@ -511,8 +519,8 @@ __global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const Bw
       }
       uint64_t segc = seg_codes(0);
       for (int q = 0; q < nq; ++q) {
-        const int b = q < ramp ? q : ramp + kSeg * (q - ramp);
-        const int len = q < ramp ? 1 : kSeg;
+        const int b = seg_begin(q);
+        const int len = seg_len(q);
         const uint64_t cur = segc;
         segc = seg_codes(q + 1);
         {
@@ -621,7 +629,9 @@ __global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const Bw
       as.seed = 0;
       as.nz = false;
       // the seed 1/L enters at row m only (the last tile's last lane)
-      const T Sseed = (last_tile && okS) ? S : (T)0;
+      // 1/L in the stored scale: 2^(-ES - EB) / S, formed as 2^(-ES - EB) (1/S) (the same
+      // value: scaling by a power of two does not change the rounding)
+      const T Sseed = (last_tile && okS) ? (T)1 / S : (T)0;
       adj_rescale<T, L, K, kBias>(as, t, Sseed, ES);
       // Partial sums, each held as (true value) x 2^-H, the lane's accumulator scale.
       // Per row r: gA (alpha_r: u(r,j+1) M(r-1,j)), gD (delta_r: I^(r,j) M(r-1,j)),
@@ -675,8 +685,8 @@ __global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const Bw
       T *const ckS = recS + (size_t)(kSeg - 2) * 32 * RW;
       bool ck_smem = false;
       for (int q = nq - 1; q >= 0; --q) {
-        const int b = q < ramp ? q : ramp + kSeg * (q - ramp);
-        const int len = q < ramp ? 1 : kSeg;
+        const int b = seg_begin(q);
+        const int len = seg_len(q);
         const uint64_t codes = segc;
         segc = seg_codes(q - 1);
         bool nzq;
@@ -747,9 +757,9 @@ __global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const Bw
                                       ain != nullptr, Eo, xo);
         pend = false;
         // reverse over the segment
-        // slots kSeg-2 and kSeg-1 are free from reverse step pf_u on (a one-step segment
+        // slots kSeg-2 and kSeg-1 are free from reverse step pf_u on (a one-step ramp segment
         // uses slot 0 only)
-        const int pf_u = (kPf && q > 0) ? (len == 1 ? 0 : len - 3) : -1;
+        const int pf_u = (kPf && q > 0) ? (len - 1 < kSeg - 3 ? len - 1 : kSeg - 3) : -1;
         for (int u2 = len - 1; u2 >= 0; --u2) {
           if (u2 == pf_u) {
             rec_copy_async<T, CKW>(ckS, ckt + (size_t)(q - 1) * 32 * CKW, lane);
