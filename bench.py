@@ -47,9 +47,9 @@ BWD_OPS_SCOPE = 25
 # subsets on the 3e11-cell step (measured best of 2^33..2^37 on GB300)
 E2E_SUBSET_CELLS = 1 << 37
 # DRAM bytes per cell of the adjoint kernel (read + written: its checkpoints), from an ncu
-# capture of wf_backward<float,16,10> on the 4.5e9-cell c3_grad batch (12.07 GB read, 15.35 GB
+# capture of wf_backward<float,16,10> on the 4.5e9-cell c3_grad batch (8.30 GB read, 10.74 GB
 # written); the c4 step's traffic is this times its cells.
-BWD_DRAM_BYTES_PER_CELL = (12.066 + 15.349) * 1e9 / 4.5e9
+BWD_DRAM_BYTES_PER_CELL = (8.298 + 10.743) * 1e9 / 4.5e9
 
 WORKLOAD_DESC = {
     "c4_persistent": "65,536 regions x 4 haplotypes x 16 reads = 2^22 pairs; read length "
