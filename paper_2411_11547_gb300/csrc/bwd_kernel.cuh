@@ -61,10 +61,10 @@ __host__ __device__ constexpr int bwd_warps_per_sm(int K, int elem, bool gq = fa
 // Most warps per block of a group's launch: the largest divisor (up to 4) of its warps per SM,
 // so that whole blocks fill the SM.
 __host__ __device__ constexpr int bwd_max_wpb(int K, int elem, bool gq = false) {
-  return bwd_warps_per_sm(K, elem, gq) % 4 == 0
-             ? 4
-             : (bwd_warps_per_sm(K, elem, gq) % 3 == 0 ? 3
-                                                       : (bwd_warps_per_sm(K, elem, gq) % 2 == 0 ? 2 : 1));
+  return bwd_warps_per_sm(K, elem, gq) % 4 == 0   ? 4
+         : bwd_warps_per_sm(K, elem, gq) % 3 == 0 ? 3
+         : bwd_warps_per_sm(K, elem, gq) % 2 == 0 ? 2
+                                                  : 1;
 }
 __host__ __device__ constexpr size_t bwd_table_bytes(int K, int elem) {
   return (size_t)kCodes * 32 * elem *
@@ -78,11 +78,14 @@ __host__ __device__ constexpr size_t bwd_rec_bytes(int K, int elem) {
 }
 // Steps whose records fit next to the table.
 __host__ __device__ constexpr int bwd_rec_fit(int K, int elem, bool gq = false) {
-  return (int)(((size_t)227 * 1024 / bwd_warps_per_sm(K, elem, gq) - 256 - bwd_table_bytes(K, elem)) /
-               bwd_rec_bytes(K, elem));
+  return (int)(((size_t)227 * 1024 / bwd_warps_per_sm(K, elem, gq) - 256 -
+                 bwd_table_bytes(K, elem)) /
+                bwd_rec_bytes(K, elem));
 }
 __host__ __device__ constexpr int bwd_seg_len(int K, int elem, bool gq = false) {
-  return bwd_rec_fit(K, elem, gq) > 8 ? 8 : (bwd_rec_fit(K, elem, gq) < 2 ? 2 : bwd_rec_fit(K, elem, gq));
+  return bwd_rec_fit(K, elem, gq) > 8   ? 8
+         : bwd_rec_fit(K, elem, gq) < 2 ? 2
+                                        : bwd_rec_fit(K, elem, gq);
 }
 __host__ __device__ constexpr size_t bwd_warp_bytes(int K, int elem, bool gq = false) {
   return bwd_table_bytes(K, elem) + (size_t)bwd_seg_len(K, elem, gq) * bwd_rec_bytes(K, elem);
@@ -886,8 +889,6 @@ __global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const Bw
               // zero elsewhere: x + 0 is not free in IEEE arithmetic)
               const T Mb0 = fma(apB, uba, fma(dlB, Ibl, zD));
               const T Mb = r == K - 1 ? Mb0 + sd : Mb0;
-              // I^(r, j): one FMA on the row-to-row chain; eps x I^(r+1, j) again for the
-              // partial
               // I^(r, j): one FMA on the row-to-row chain
               const T Ib = fma(eiB, Ibl, r == K - 1 ? uba + sd : uba);
               const T Dn = uba + (GQ ? er[r] : eps) * as.Db[r];            // D^(r, j)
