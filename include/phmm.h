@@ -114,11 +114,18 @@ typedef struct phmm_options {
                           at most 2^30 cells, captured when a call repeats the previous
                           call's pointers (their kernel-time events are then not recorded) */
   int32_t warps_per_block; /* 1..4 warps per block (0 = 4) */
-  int32_t bin_rows[PHMM_MAX_READ_LEN / 4 + 1]; /* optional read-length -> group table */
+  int32_t bin_rows[PHMM_MAX_READ_LEN / 4 + 1]; /* optional read-length -> group table: entry
+                          (m + 3) / 4 is the group of reads of length m, as an index
+                          li * 17 + (rows - 4) with lanes 4 << li (li = 0..3) and rows per lane
+                          4..20 (the forward is built for even rows, the adjoint for 4-12 and
+                          some others: see bwd_rows); -1 or an unbuilt group: the default */
   int32_t bin_table_valid; /* 1 if bin_rows holds a table */
   int32_t adjoint_rescue;  /* 1: adjoints out of the FP32 range are redone in FP64; 0: NaN;
                               2: every pair's adjoint in FP64 (reference gradients, slower) */
-  int32_t bwd_rows[PHMM_MAX_READ_LEN / 4 + 1]; /* optional read-length -> adjoint group table */
+  int32_t bwd_rows[PHMM_MAX_READ_LEN / 4 + 1]; /* optional read-length -> adjoint group table
+                          (indices as bin_rows; adjoint groups: rows 4, 6, 8, 10, 12 with any
+                          lanes, 16 x 14, 32 x 16, and 4 x 9/11, 8 x 7/9/11, 16 x 9/11/13,
+                          32 x 9) */
   int32_t bwd_table_valid; /* 1 if bwd_rows holds a table */
   int32_t bwd_warps_per_block; /* adjoint launches: 1..4 (0 = warps_per_block) */
 } phmm_options;

@@ -79,6 +79,7 @@ size_t reduce_scratch_bytes_aligned(int64_t P, int64_t R);
 
 static BwdKernel bwd_kernel32(int L, int K, bool gq = false) {
   if (gq) return bwd32_gq(L, K);
+  if (K % 2 == 1) return L <= 8 ? bwd32_odd_lo(L, K) : bwd32_odd_hi(L, K);
   switch (L) {
     case 4:
     case 8: return bwd32_lo(L, K);

@@ -41,7 +41,9 @@ __host__ __device__ constexpr int vecw(int elem) { return 16 / elem; }
 __host__ __device__ constexpr int ck_w(int K, int elem) {
   return (2 * K + 5 + vecw(elem) - 1) / vecw(elem) * vecw(elem);
 }
-__host__ __device__ constexpr int rec_w(int K, int elem) { return (void)elem, 2 * K; }
+__host__ __device__ constexpr int rec_w(int K, int elem) {
+  return (2 * K + vecw(elem) - 1) / vecw(elem) * vecw(elem);
+}
 template <typename T>
 __host__ __device__ constexpr int ck_width(int K) { return ck_w(K, (int)sizeof(T)); }
 template <typename T>
@@ -748,6 +750,8 @@ __global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const Bw
               rec[r] = st.M[r];
               rec[K + r] = st.D[r];
             }
+#pragma unroll
+            for (int k = 2 * K; k < RW; ++k) rec[k] = 0;  // odd rows: padding to 16 bytes
             rec_store<T, RW>(recS + (size_t)u2 * 32 * RW, lane, rec);
             recI[u2 * 32 + lane] = st.I[0];
           }
@@ -1210,11 +1214,14 @@ __global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const Bw
 using BwdKernel = void (*)(const BwdArgs);
 
 // Instantiation tables (nullptr where a group is not built).  FP32: lanes 4..32, rows per
-// lane 4/6/8/10/12 (also 14 with 16 lanes, and 16 with 32 lanes for reads up to 512); FP64
-// hand-off groups: 32 lanes x rows 4/8/16.
+// lane 4/6/8/10/12 (also 14 with 16 lanes, and 16 with 32 lanes for reads up to 512), and
+// odd rows where they fit a read-length range more closely: 4 x 9/11, 8 x 7/9/11,
+// 16 x 9/11/13, 32 x 9; FP64 hand-off groups: 32 lanes x rows 4/8/16.
 BwdKernel bwd32_lo(int L, int K);   // L in {4, 8}
 BwdKernel bwd32_mid(int L, int K);  // L = 16
 BwdKernel bwd32_hi(int L, int K);   // L = 32
+BwdKernel bwd32_odd_lo(int L, int K);  // odd rows, L in {4, 8}
+BwdKernel bwd32_odd_hi(int L, int K);  // odd rows, L in {16, 32}
 BwdKernel bwd64_table(int K);       // L = 32
 // per-base gap-continuation track: (16,4) (16,8) (32,8) (32,12) (32,16); FP64 32 x 4/8/16
 BwdKernel bwd32_gq(int L, int K);

@@ -114,6 +114,11 @@ static FwdKernel get64(int cfg64, bool ext, bool gq = false) {
 }
 
 size_t fwd32_smem(int cfg, int block) { return (block / 32) * table_warp_bytes(cfg_rows(cfg), 4); }
+// 1 if the FP32 forward kernels (both first lines) are built for group `cfg`.
+int fwd_cfg_supported(int cfg) {
+  return cfg >= 0 && cfg < kNumCfg32 && get32(cfg, true) != nullptr &&
+         get32(cfg, false) != nullptr;
+}
 size_t fwd64_smem(int cfg64, int block) {
   return (block / 32) * table_warp_bytes(rows64(cfg64), 8);
 }
@@ -439,7 +444,7 @@ int phmm_plan_create(const phmm_batch *batch, const phmm_options *opt, void *str
     }
     if (o.bin_table_valid) {
       const int e = o.bin_rows[(std::max(m, 1) + 3) / 4];
-      if (e >= 0 && e < kNumCfg32 && cfg_lanes(e) * cfg_rows(e) >= m) c = e;
+      if (fwd_cfg_supported(e) && cfg_lanes(e) * cfg_rows(e) >= m) c = e;
     }
     pl->cfg_of_m[m] = c;
   }

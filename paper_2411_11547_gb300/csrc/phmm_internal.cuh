@@ -18,12 +18,15 @@ constexpr float kMinAccepted32 = 1e-28f;                   // scaled FP32 sum be
 constexpr double kMinAccepted64 = 1e-290;                  // scaled FP64 sum below: extended
 
 // Fixed-function FP32 wavefront groups: lanes per pair x rows per lane.
-// cfg = li * 9 + ki with lanes 4 << li (4, 8, 16, 32) and rows 4 + 2 ki (4, 6, .., 20).
-constexpr int kNumCfg32 = 36;
-__host__ __device__ constexpr int cfg_lanes(int cfg) { return 4 << (cfg / 9); }
-__host__ __device__ constexpr int cfg_rows(int cfg) { return 4 + 2 * (cfg % 9); }
+// cfg = li * 17 + (rows - 4) with lanes 4 << li (4, 8, 16, 32) and rows 4 .. 20.  The forward
+// kernels are built for even rows; the adjoint also for some odd ones (a closer fit of the
+// read length).  Group tables of the options hold these indices.
+constexpr int kRowsPerLanes = 17;
+constexpr int kNumCfg32 = 4 * kRowsPerLanes;
+__host__ __device__ constexpr int cfg_lanes(int cfg) { return 4 << (cfg / kRowsPerLanes); }
+__host__ __device__ constexpr int cfg_rows(int cfg) { return 4 + cfg % kRowsPerLanes; }
 __host__ __device__ constexpr int cfg_index(int L, int K) {
-  return (L == 4 ? 0 : L == 8 ? 1 : L == 16 ? 2 : 3) * 9 + (K - 4) / 2;
+  return (L == 4 ? 0 : L == 8 ? 1 : L == 16 ? 2 : 3) * kRowsPerLanes + (K - 4);
 }
 
 // FP64 rescue groups: 32 lanes x {4, 8, 16} rows (reads up to 128 / 256 / 512).

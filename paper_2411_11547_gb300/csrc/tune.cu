@@ -17,6 +17,7 @@
 
 namespace phmm {
 int bwd_cfg_supported(int cfg);
+int fwd_cfg_supported(int cfg);
 int bwd_default_cfg(int m);
 int default_cfg_of_m(int m);
 }
@@ -272,6 +273,7 @@ extern "C" int phmm_autotune(const phmm_batch *batch, phmm_options *opt, int whi
       for (int cfg = 0; cfg < kNumCfg32; ++cfg) {
         const int cap = cfg_lanes(cfg) * cfg_rows(cfg);
         if (cap < hi || cap > std::max(2 * hi, 64)) continue;
+        if (pass == 1 && !fwd_cfg_supported(cfg)) continue;
         if (pass == 2 && !bwd_cfg_supported(cfg)) continue;
         phmm_options o = *opt;
         o.binning = 1;

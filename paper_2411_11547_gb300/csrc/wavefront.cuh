@@ -101,32 +101,26 @@ __device__ __forceinline__ void store_vec<double, 2>(double *dst, const double *
   *reinterpret_cast<double2 *>(dst) = make_double2(v[0], v[1]);
 }
 
-// K rows of a lane's emission row: 128-bit loads, and a 64-bit load for two leftover floats.
+// K rows of a lane's emission row: 128-bit loads.  The row is padded to whole vectors, so a
+// partial last vector is read with one 128-bit load too (a 64-bit load at the odd 16-byte
+// lane stride would put two lanes of a half-warp on the same bank).
 template <typename T, int K>
 __device__ __forceinline__ void load_rows(const T *src, T (&e)[K]) {
   constexpr int VW = 16 / sizeof(T);
 #pragma unroll
-  for (int r = 0; r + VW <= K; r += VW) {
+  for (int r = 0; r < K; r += VW) {
     if constexpr (sizeof(T) == 4) {
-      float4 v = *reinterpret_cast<const float4 *>(src + r);
+      const float4 v = *reinterpret_cast<const float4 *>(src + r);
       e[r] = v.x;
-      e[r + 1] = v.y;
-      e[r + 2] = v.z;
-      e[r + 3] = v.w;
+      if (r + 1 < K) e[r + 1] = v.y;
+      if (r + 2 < K) e[r + 2] = v.z;
+      if (r + 3 < K) e[r + 3] = v.w;
     } else {
-      double2 v = *reinterpret_cast<const double2 *>(src + r);
+      const double2 v = *reinterpret_cast<const double2 *>(src + r);
       e[r] = v.x;
-      e[r + 1] = v.y;
+      if (r + 1 < K) e[r + 1] = v.y;
     }
   }
-  if constexpr (K % VW == 2 && sizeof(T) == 4) {
-    // the row is padded to a whole vector: one 128-bit load (a 64-bit load at the odd 16-byte
-    // lane stride would put two lanes of a half-warp on the same bank)
-    float4 v = *reinterpret_cast<const float4 *>(src + K - 2);
-    e[K - 2] = v.x;
-    e[K - 1] = v.y;
-  }
-  static_assert(K % VW == 0 || (K % VW == 2 && sizeof(T) == 4), "rows per lane");
 }
 
 __device__ __forceinline__ double qual_at(const void *q, int f32, int64_t g) {

@@ -16,6 +16,17 @@ PHMM_OK, PHMM_EINVAL, PHMM_ETOOLONG, PHMM_ENOMEM, PHMM_ECUDA, PHMM_ESTATE = 0, -
 PHMM_EGUARD = -6  # debug builds: a guard region or a kernel index check failed
 PHMM_MAX_READ_LEN = 512
 FLAG_FP32, FLAG_RESCUED64, FLAG_EXTENDED, FLAG_INVALID = 1, 2, 4, 8
+
+
+def cfg_index(lanes: int, rows: int) -> int:
+    """Group index held by the options' bin_rows / bwd_rows tables (lanes 4/8/16/32, rows per
+    lane 4..20), as the library encodes it."""
+    return {4: 0, 8: 1, 16: 2, 32: 3}[lanes] * 17 + (rows - 4)
+
+
+def cfg_shape(c: int) -> tuple:
+    """(lanes, rows) of group index c."""
+    return 4 << (c // 17), 4 + c % 17
 QUAL_U8, QUAL_F32 = 0, 1
 FIRST_PLAIN32, FIRST_EXT32 = 0, 1
 

@@ -221,7 +221,8 @@ def test_autograd_function(phmm):
     assert abs(float(gcp.grad) - wg) <= RTOL * abs(wg) + 1e-9
 
 
-BWD_SHAPES = [(L, K) for L in (4, 8, 16, 32) for K in (4, 6, 8, 10, 12)] + [(16, 14), (32, 16)]
+BWD_SHAPES = ([(L, K) for L in (4, 8, 16, 32) for K in (4, 6, 8, 10, 12)] + [(16, 14), (32, 16)]
+              + [(4, 9), (4, 11), (8, 7), (8, 9), (8, 11), (16, 9), (16, 11), (16, 13), (32, 9)])
 
 
 @pytest.mark.parametrize("L,K", BWD_SHAPES)
@@ -232,7 +233,7 @@ def test_every_backward_shape(phmm, L, K):
     b = synth.random_pairs(300 + cap + K, 24, (max(1, cap // 3), cap), (1, 260), related=0.6,
                            qual_dtype=np.float32)
     assert np.diff(b["read_off"]).max() <= cap
-    c = {4: 0, 8: 1, 16: 2, 32: 3}[L] * 9 + (K - 4) // 2
+    c = phmm.cfg_index(L, K)
     dy = np.random.default_rng(cap).uniform(-1, 1, len(b["pair_read"]))
     check_against_oracle(phmm, b, dy, bwd_rows=[c] * 129)
 

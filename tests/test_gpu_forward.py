@@ -335,5 +335,5 @@ def test_metamorphic_order_blocks_and_bins(phmm):
         got, flags, _ = run(phmm, pb, warps_per_block=wpb)
         assert np.array_equal(got, base[perm]) and np.array_equal(flags, bflags[perm])
     # bin edges moved: reads of every length scored by the wider 32 x 16 group
-    got, flags, _ = run(phmm, b, bin_rows=[3 * 9 + 6] * 129)
+    got, flags, _ = run(phmm, b, bin_rows=[phmm.cfg_index(32, 16)] * 129)
     assert np.max(np.abs(got - base)) <= 2e-4
