@@ -10,7 +10,8 @@ from test_gpu_backward import grad_close, RTOL
 pytestmark = pytest.mark.gpu
 
 # adjoint groups with odd rows per lane
-ODD_BWD = ((4, 9), (4, 11), (8, 7), (8, 9), (8, 11), (16, 9), (16, 11), (16, 13), (32, 9))
+ODD_BWD = ((4, 9), (4, 11), (8, 7), (8, 9), (8, 11), (16, 7), (16, 9), (16, 11), (16, 13),
+           (32, 9))
 
 
 @pytest.fixture(scope="module")
