@@ -43,9 +43,10 @@ BWD_OPS_PER_CELL = 22
 # roofline line uses these; the reduced counts above are reported beside them.
 FWD_OPS_SCOPE = 7
 BWD_OPS_SCOPE = 25
-# subset size of the end-to-end host call (phmm_grad_host): with the ramp at both ends about 7
-# subsets on the 3e11-cell step (measured best of 2^33..2^37 on GB300)
-E2E_SUBSET_CELLS = 1 << 37
+# subset size of the end-to-end host call (phmm_grad_host): with the ramp at both ends about 5
+# subsets on the 3e11-cell step (measured on GB300, per step: 2^35 739, 2^36 734, 2^37 725,
+# 2^38 721 ms)
+E2E_SUBSET_CELLS = 1 << 38
 # DRAM bytes per cell of the adjoint kernel (read + written: its checkpoints), from an ncu
 # capture of wf_backward<float,16,10> on the 4.5e9-cell c3_grad batch (8.30 GB read, 10.74 GB
 # written); the c4 step's traffic is this times its cells.

@@ -447,7 +447,7 @@ def score_host(batch, opts: Options | None = None, subset_cells: int = 1 << 33):
     return out, flags
 
 
-def grad_host(batch, dL, opts: Options | None = None, subset_cells: int = 1 << 37, out=None):
+def grad_host(batch, dL, opts: Options | None = None, subset_cells: int = 1 << 38, out=None):
     """phmm_grad_host: log10 L, flags and d(loss)/d(base_q, ins_q, del_q, gcp) (numpy) of a
     batch held in host memory, given dL = d(loss)/d(log10 L) per pair (host), in pipelined
     subsets of about `subset_cells` cells.  `out`: optional preallocated
