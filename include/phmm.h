@@ -125,7 +125,7 @@ typedef struct phmm_options {
   int32_t bwd_rows[PHMM_MAX_READ_LEN / 4 + 1]; /* optional read-length -> adjoint group table
                           (indices as bin_rows; adjoint groups: rows 4, 6, 8, 10, 12 with any
                           lanes, 16 x 14, 32 x 16, and 4 x 9/11, 8 x 7/9/11, 16 x 7/9/11/13,
-                          32 x 9) */
+                          32 x 7/9) */
   int32_t bwd_table_valid; /* 1 if bwd_rows holds a table */
   int32_t bwd_warps_per_block; /* adjoint launches: 1..4 (0 = warps_per_block) */
 } phmm_options;

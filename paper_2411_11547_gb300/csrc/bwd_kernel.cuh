@@ -1216,7 +1216,7 @@ using BwdKernel = void (*)(const BwdArgs);
 // Instantiation tables (nullptr where a group is not built).  FP32: lanes 4..32, rows per
 // lane 4/6/8/10/12 (also 14 with 16 lanes, and 16 with 32 lanes for reads up to 512), and
 // odd rows where they fit a read-length range more closely: 4 x 9/11, 8 x 7/9/11,
-// 16 x 7/9/11/13, 32 x 9; FP64 hand-off groups: 32 lanes x rows 4/8/16.
+// 16 x 7/9/11/13, 32 x 7/9; FP64 hand-off groups: 32 lanes x rows 4/8/16.
 BwdKernel bwd32_lo(int L, int K);   // L in {4, 8}
 BwdKernel bwd32_mid(int L, int K);  // L = 16
 BwdKernel bwd32_hi(int L, int K);   // L = 32

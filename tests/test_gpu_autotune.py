@@ -11,7 +11,7 @@ pytestmark = pytest.mark.gpu
 
 # adjoint groups with odd rows per lane
 ODD_BWD = ((4, 9), (4, 11), (8, 7), (8, 9), (8, 11), (16, 7), (16, 9), (16, 11), (16, 13),
-           (32, 9))
+           (32, 7), (32, 9))
 
 
 @pytest.fixture(scope="module")

@@ -223,7 +223,7 @@ def test_autograd_function(phmm):
 
 BWD_SHAPES = ([(L, K) for L in (4, 8, 16, 32) for K in (4, 6, 8, 10, 12)] + [(16, 14), (32, 16)]
               + [(4, 9), (4, 11), (8, 7), (8, 9), (8, 11), (16, 7), (16, 9), (16, 11), (16, 13),
-                 (32, 9)])
+                 (32, 7), (32, 9)])
 
 
 @pytest.mark.parametrize("L,K", BWD_SHAPES)
