@@ -1095,7 +1095,8 @@ __global__ void __maxnreg__(bwd_max_regs(K, sizeof(T), GQ)) wf_backward(const Bw
         wh |= __shfl_xor_sync(FULL, wh, o, L);
         wf |= __shfl_xor_sync(FULL, wf, o, L);
       }
-      // d ln L / d eps = gE - gS / beta (beta = 1 - eps); d eps / d gcp = -(ln 10 / 10) eps
+      // d ln L / d eps = gEs - gSs / beta (gSs: the beta count; beta = 1 - eps);
+      // d eps / d gcp = -(ln 10 / 10) eps
       // (with a per-base track gSs already holds the sum of the rows' d log10 L / d gcp_r)
       const T dgcp_l = GQ ? gSs : -(gEs - gSs / beta) * eps * (T)0.1;
       if (!(fabs(dgcp_l) < (T)1e30)) hs_any = 1;
